@@ -1,0 +1,218 @@
+/*
+ * mpsolve.h -- C ABI of the GB300 mixed-precision iterative-refinement solver.
+ *
+ * Method: Baboulin, Buttari, Dongarra, Kurzak, Langou, Langou, Luszczek,
+ * Tomov, "Accelerating Scientific Computations with Mixed Precision
+ * Algorithms".  The problem statement is Section 2.1: given A (n x n) and
+ * b in FP64, factor PA = LU in a lower precision, then refine
+ * x_k = x_{k-1} + z_k with the residual r_k = b - A x_{k-1} and the update
+ * computed in FP64 (Algorithm 1).  Section 3.1.1 maps the steps onto
+ * LAPACK's SGETRF/SGETRS (general) and SPOTRF/SPOTRS (SPD); Section 4 gives
+ * the fallback to a full FP64 solve when kappa(A) * eps_s >= 1.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major with a leading dimension (LAPACK layout).
+ *   - Pointers named d* are DEVICE pointers owned by the caller; pointers
+ *     named h* are HOST pointers owned by the caller.  The library never
+ *     allocates device memory: scratch space comes from the caller through
+ *     (work, work_bytes), sized by the matching *_workspace_bytes query.
+ *   - A and B are read-only.  X is output-only and must not overlap A or B.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; a call returns after reading back the
+ *     small status block (iterations, flags), so X is valid on return.
+ *   - Pivots are LAPACK style: int32, 1-based, row i was exchanged with row
+ *     ipiv[i], applied for i = 0..n-1 in order.
+ *   - Return value: 0 success; -i if argument i (1-based) is illegal
+ *     (including a workspace that is too small); +i if the FP64 fallback
+ *     factorization met an exact zero pivot U(i,i) (A singular); values
+ *     <= -1000 report a CUDA error (-1000 - cudaError_t); mp_last_error()
+ *     gives the text.
+ *   - The library runs on the current CUDA device only and needs sm_103a.
+ *     Not thread-safe for concurrent calls that share a workspace.
+ */
+#ifndef MPSOLVE_H
+#define MPSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MP_API __attribute__((visibility("default")))
+#else
+#define MP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Precision of the O(n^3) factorization (Algorithm 1 step 1 at eps_s). */
+typedef enum {
+    MP_PREC_FP32 = 0,   /* all factorization arithmetic in FP32 (the paper's single) */
+    MP_PREC_TF32X3 = 1, /* trailing update on tensor cores, 3 TF32 products (~FP32 accuracy) */
+    MP_PREC_BF16 = 2,   /* trailing-update operands rounded to bfloat16, FP32 accumulation */
+    MP_PREC_FP16 = 3,   /* trailing-update operands rounded to binary16, FP32 accumulation */
+    MP_PREC_E4M3 = 4    /* reserved: FP8 E4M3 with per-block power-of-two scales */
+} mp_prec;
+
+/* Refinement scheme. */
+typedef enum {
+    MP_REFINE_CLASSICAL = 0, /* Algorithm 1 (Section 2.1) */
+    MP_REFINE_GMRES = 1,     /* FGMRES preconditioned by the low-precision LU
+                                (right preconditioning, Section 2.2; Section 4) */
+    MP_REFINE_AUTO = 2       /* classical, switching to GMRES when it stalls */
+} mp_refine;
+
+/* Result flags (mp_stats.flags). */
+#define MP_FLAG_FALLBACK 1u       /* the answer came from the FP64 re-factorization */
+#define MP_FLAG_STALLED 2u        /* classical refinement stalled */
+#define MP_FLAG_LOWP_BREAKDOWN 4u /* zero/non-finite low-precision pivot or non-positive
+                                     Cholesky pivot */
+#define MP_FLAG_NONFINITE_INPUT 8u
+#define MP_FLAG_TIMEOUT 16u       /* a bounded device-side wait gave up */
+#define MP_FLAG_GMRES_USED 32u
+#define MP_FLAG_NOT_CONVERGED 64u /* no convergence and fallback disabled */
+
+typedef struct {
+    int prec;            /* mp_prec, default MP_PREC_FP32 */
+    int refine;          /* mp_refine, default MP_REFINE_CLASSICAL */
+    int itermax;         /* maximum corrections (default 30; 30 unconverged = failure, Section 4) */
+    double tol;          /* backward-error target per column (default 1e-14) */
+    int gmres_restart;   /* inner steps per GMRES cycle (default 30) */
+    double gmres_tol;    /* relative inner residual target (default 1e-6) */
+    double stall_ratio;  /* stall if ||z_k|| > stall_ratio * ||z_{k-1}|| (default 0.5) */
+    int allow_fallback;  /* re-factor in FP64 on breakdown/stall/non-convergence (default 1) */
+    int nb_outer;        /* outer block width of the factorization (0 = auto) */
+    int nb_inner;        /* reserved (0 = auto) */
+} mp_opts;
+
+typedef struct {
+    int iter;            /* corrections applied (>= 0), or -1 if the FP64 fallback answered */
+    unsigned flags;      /* MP_FLAG_* */
+    int info;            /* low-precision factorization: first zero pivot (1-based) or 0 */
+    int n_precond;       /* applications of the low-precision solve (LU)^{-1} P */
+    double bwd_err;      /* max over columns of ||r||inf / (||A||inf ||x||inf + ||b||inf),
+                            as seen by the last convergence test */
+    int nhist;           /* entries in hist */
+    double hist[32];     /* max backward error before each correction */
+    float ms_convert, ms_factor, ms_refine, ms_fallback; /* phase times (0 unless timing on) */
+} mp_stats;
+
+/* Fills *opts with the defaults listed above. */
+MP_API void mp_default_opts(mp_opts *opts);
+
+/* Text of the last error raised on this thread ("" if none). */
+MP_API const char *mp_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Drivers (Algorithm 1, Section 2.1; LAPACK mapping Section 3.1.1).
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace mp_gesv needs for (n, nrhs, opts). */
+MP_API size_t mp_gesv_workspace_bytes(int n, int nrhs, const mp_opts *opts);
+
+/* Solve A X = B for general A: factor PA = LU at opts->prec, refine in
+ * FP64 until every column's normwise backward error <= opts->tol, or fall
+ * back to an FP64 LU solve.  dA: n x n FP64 (lda >= max(1,n)); dB, dX:
+ * n x nrhs FP64; dipiv: n int32 (output, LAPACK 1-based; the FP64 pivots
+ * when the fallback answered); work: device scratch of work_bytes >=
+ * mp_gesv_workspace_bytes().  stats may be NULL.  Arguments are numbered
+ * 1..14 in order for the -i error convention. */
+MP_API int mp_gesv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
+            double *dX, int ldx, int32_t *dipiv, void *work, size_t work_bytes,
+            const mp_opts *opts, mp_stats *stats, void *stream);
+
+/* Same as mp_gesv but with HOST A, B, X and ipiv: the call copies A and B to
+ * the device workspace, solves, and copies X and ipiv back (the copies are
+ * part of the call).  work must hold mp_gesv_host_workspace_bytes(). */
+MP_API size_t mp_gesv_host_workspace_bytes(int n, int nrhs, const mp_opts *opts);
+MP_API int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const double *hB, int ldb,
+                 double *hX, int ldx, int32_t *hipiv, void *work, size_t work_bytes,
+                 const mp_opts *opts, mp_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Steps of the hot path, exposed for testing and for callers that keep
+ * the factors (Section 3.1.1: SGETRF, SGETRS, DGEMM residual, DAXPY).
+ * The low-precision factors live in the caller's workspace as W, an FP32
+ * ROW-major n x ldw array (ldw = mp_factor_ld(n)).
+ * ------------------------------------------------------------------------ */
+
+/* Leading dimension (in elements) of the row-major FP32 factor array W. */
+MP_API int mp_factor_ld(int n);
+
+/* Bytes of workspace needed by mp_getrf_lowp beyond W itself. */
+MP_API size_t mp_getrf_workspace_bytes(int n, const mp_opts *opts);
+
+/* W = fl32(A) stored row-major (W[i*ldw + j] = fl32(A[i + j*lda])), and
+ * *d_anorm (device double) = ||A||_inf.  Sets MP_FLAG_NONFINITE_INPUT in
+ * *d_flags (device uint32, OR-ed) if A has a NaN/Inf. */
+MP_API int mp_convert(int n, const double *dA, int lda, float *dW, int ldw,
+               double *d_anorm, uint32_t *d_flags, void *work, size_t work_bytes,
+               void *stream);
+
+/* In-place LU with partial pivoting of the row-major FP32 W (n x n, ldw),
+ * trailing updates at opts->prec.  dipiv: n int32 LAPACK 1-based.
+ * On return *info (host) = first zero pivot (1-based) or 0, and *flags
+ * (host) has MP_FLAG_LOWP_BREAKDOWN if a pivot was zero or non-finite. */
+MP_API int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp_opts *opts,
+                  void *work, size_t work_bytes, int *info, uint32_t *flags, void *stream);
+
+/* Solve with the FP32 factors (Algorithm 1 steps 5-6):
+ * dZ = s * U^{-1} L^{-1} P (dR / s) computed in FP32, s = 2^ceil(log2 ||r||inf)
+ * per column (exact scaling), returned in FP64.  dR, dZ: n x nrhs FP64
+ * column-major (nrhs <= 8).  work must hold mp_getrs_workspace_bytes(n, nrhs). */
+MP_API size_t mp_getrs_workspace_bytes(int n, int nrhs);
+MP_API int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const int32_t *dipiv,
+                  const double *dR, int ldr, double *dZ, int ldz, void *work,
+                  size_t work_bytes, void *stream);
+
+/* Trailing update of the blocked factorization (the O(n^3) step of
+ * Algorithm 1 step 1, Section 2.1): C[M x N] -= fl_p(L)[M x K] * fl_p(U)[K x N]
+ * with all three arrays FP32 ROW-major on the device (ldl >= K, ldu >= N,
+ * ldc >= N; ldl, ldu, ldc multiples of 4).  prec: MP_PREC_FP32 (plain FP32
+ * FMA on CUDA cores), MP_PREC_BF16 / MP_PREC_FP16 (operands rounded to
+ * nearest even, FP32 accumulation on tcgen05 tensor cores).  work must hold
+ * mp_lowp_gemm_workspace_bytes(M, N, K, prec). */
+MP_API size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec);
+MP_API int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl,
+                               const float *dU, int ldu, float *dC, int ldc, void *work,
+                               size_t work_bytes, void *stream);
+
+/* dR = dB - dA dX in FP64 (Algorithm 1 step 4), all n x nrhs column-major.
+ * work must hold mp_residual_workspace_bytes(n, nrhs). */
+MP_API size_t mp_residual_workspace_bytes(int n, int nrhs);
+MP_API int mp_residual(int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
+                const double *dB, int ldb, double *dR, int ldr, void *work,
+                size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used by the benchmark).
+ * ------------------------------------------------------------------------ */
+
+/* Kernel classes timed by the profiler. */
+#define MP_KC_PANEL 0      /* pivoted panel (cluster kernel) */
+#define MP_KC_ROWMOVES 1   /* composed row exchanges */
+#define MP_KC_TRSM 2       /* U12 = L11^{-1} A12 (small solves + FP32 GEMMs) */
+#define MP_KC_UPDATE 3     /* trailing update A22 -= L21 U12 (outer level) */
+#define MP_KC_PANELGEMM 4  /* FP32 updates inside the recursive panel */
+#define MP_KC_TRSV 5       /* triangular solves with the factors */
+#define MP_KC_RESIDUAL 6   /* FP64 residual */
+#define MP_KC_COUNT 7
+
+/* Enables (mask != 0) or disables event timing of the kernel classes in
+ * mask (bit i = class i) on the stream each kernel is launched on, and
+ * clears the accumulated records. */
+MP_API void mp_profile_enable(unsigned mask);
+/* Waits for the recorded events and returns, per class, the summed kernel
+ * time (ms), the number of timed launches and the summed algorithmic work of
+ * those launches (flops for PANEL/TRSM/UPDATE/PANELGEMM, bytes for the
+ * others).  Arrays have MP_KC_COUNT entries.  Returns 0 or a CUDA error code. */
+MP_API int mp_profile_collect(double *ms, long long *launches, double *work);
+/* Number of kernels this library has launched in this process so far. */
+MP_API long long mp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPSOLVE_H */

@@ -408,11 +408,14 @@ void or_bwd_err(int n, int nrhs, const double *A, int lda, const double *X,
 /*                                                                      */
 /* factor_prec: 32 = IEEE single (the paper's method), 64 = double      */
 /* (classical refinement used to produce the reference solution).       */
-/* The convergence test (the paper leaves it open) is normwise backward */
-/* error <= tol per column, tested on x_{k-1} before z_k is computed.   */
-/* iter counts the corrections applied; the stall test is the ratio    */
-/* ||z_k|| / ||z_{k-1}|| > stall_ratio for k >= 2 (Demmel et al. 2006,  */
-/* cited in Section 2.1).  On breakdown, stall or non-convergence the   */
+/* Convergence test (the paper leaves it open, Section 2.1; Section 3   */
+/* stops "as accurate as the full double precision" solve): x_k is      */
+/* accepted when, per column, the normwise backward error is <= tol AND */
+/* x_k has reached the FP64 floor: bwd == 0, or the last correction is  */
+/* <= 4 u64 ||x_k||, or the corrections stopped shrinking (||z_k|| >     */
+/* stall_ratio ||z_{k-1}||, k >= 2).  The same shrink test with bwd >   */
+/* tol is a stall (Demmel et al. 2006, cited in Section 2.1).  iter     */
+/* counts the corrections applied.  On breakdown, stall or non-convergence the   */
 /* routine resorts to the FP64 solve (Section 4: "resort to the         */
 /* standard double precision solver") when allow_fallback != 0.         */
 /* The low-precision solves scale r by s = 2^ceil(log2 ||r||_inf)       */
@@ -455,6 +458,7 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
     double *znorm_prev = (double *)calloc((size_t)(nrhs > 0 ? nrhs : 1), sizeof(double));
     int nh = 0;
     int converged = 0, fail = 0;
+    double *zlast = (double *)calloc((size_t)(nrhs > 0 ? nrhs : 1), sizeof(double));
 
     for (int c = 0; c < nrhs; ++c)
         if (!all_finite(&B[IDX(0, c, ldb)], (size_t)n)) flags |= OR_NONFINITE;
@@ -484,11 +488,19 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                 for (int i = 0; i < n; ++i) X[IDX(i, c, ldx)] = (double)Z[IDX(i, c, n)] * s;
             }
             double anorm = or_dnorm_inf(n, n, A, lda);
+            /* ||z|| of the last and the previous correction; x_0 counts as the
+             * first "correction" from zero */
+            for (int c = 0; c < nrhs; ++c) {
+                double xn = 0.0;
+                for (int i = 0; i < n; ++i) xn = fmax(xn, fabs(X[IDX(i, c, ldx)]));
+                zlast[c] = xn;
+                znorm_prev[c] = 0.0;
+            }
             for (;;) {
                 /* step 4: r = b - A x (FP64) and the convergence check */
                 or_dresidual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
                 double worst = 0.0;
-                int done = 1, nonfinite = 0;
+                int done = 1, nonfinite = 0, stalled = 0;
                 for (int c = 0; c < nrhs; ++c) {
                     double rn = 0.0, xn = 0.0, bn = 0.0;
                     for (int i = 0; i < n; ++i) {
@@ -499,15 +511,24 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     }
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
-                    if (!(bwd[c] <= tol)) done = 0;
+                    int stagnant = iter >= 2 && zlast[c] > stall_ratio * znorm_prev[c];
+                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    if (!(bwd[c] <= tol && at_floor)) done = 0;
+                    if (!(bwd[c] <= tol) && stagnant) stalled = 1;
                     if (bwd[c] > worst || isnan(bwd[c])) worst = bwd[c];
                 }
                 if (nh < 32) hist[nh++] = worst;
                 if (nonfinite) { flags |= OR_BREAKDOWN; fail = 1; break; }
                 if (done) { converged = 1; break; }
-                if (iter >= itermax) { fail = 1; break; }
+                if (stalled) { flags |= OR_STALLED; fail = 1; break; }
+                if (iter >= itermax) {
+                    /* out of corrections: converged only if every column meets tol */
+                    int ok = 1;
+                    for (int c = 0; c < nrhs; ++c) if (!(bwd[c] <= tol)) ok = 0;
+                    if (ok) converged = 1; else fail = 1;
+                    break;
+                }
                 /* steps 5-7 */
-                int stalled = 0;
                 for (int c = 0; c < nrhs; ++c) {
                     double rn = 0.0;
                     for (int i = 0; i < n; ++i) rn = fmax(rn, fabs(R[IDX(i, c, n)]));
@@ -520,11 +541,10 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                         X[IDX(i, c, ldx)] += z;
                         zn = fmax(zn, fabs(z));
                     }
-                    if (iter >= 1 && zn > stall_ratio * znorm_prev[c] && !(bwd[c] <= tol)) stalled = 1;
-                    znorm_prev[c] = zn;
+                    znorm_prev[c] = zlast[c];
+                    zlast[c] = zn;
                 }
                 ++iter;
-                if (stalled) { flags |= OR_STALLED; fail = 1; break; }
             }
         }
         free(W);
@@ -540,6 +560,12 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                 for (int i = 0; i < n; ++i) X[IDX(i, c, ldx)] = B[IDX(i, c, ldb)];
             for (int c = 0; c < nrhs; ++c) or_dgetrs(n, 1, F, n, ipiv, &X[IDX(0, c, ldx)], ldx);
             double anorm = or_dnorm_inf(n, n, A, lda);
+            for (int c = 0; c < nrhs; ++c) {
+                double xn = 0.0;
+                for (int i = 0; i < n; ++i) xn = fmax(xn, fabs(X[IDX(i, c, ldx)]));
+                zlast[c] = xn;
+                znorm_prev[c] = 0.0;
+            }
             for (;;) {
                 or_dresidual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
                 int done = 1;
@@ -553,14 +579,22 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     }
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
-                    if (!(bwd[c] <= tol)) done = 0;
+                    int stagnant = iter >= 2 && zlast[c] > stall_ratio * znorm_prev[c];
+                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    if (!(bwd[c] <= tol && at_floor)) done = 0;
                     if (bwd[c] > worst || isnan(bwd[c])) worst = bwd[c];
                 }
                 if (nh < 32) hist[nh++] = worst;
                 if (done || iter >= itermax) break;
                 for (int c = 0; c < nrhs; ++c) {
                     or_dgetrs(n, 1, F, n, ipiv, &R[IDX(0, c, n)], n);
-                    for (int i = 0; i < n; ++i) X[IDX(i, c, ldx)] += R[IDX(i, c, n)];
+                    double zn = 0.0;
+                    for (int i = 0; i < n; ++i) {
+                        X[IDX(i, c, ldx)] += R[IDX(i, c, n)];
+                        zn = fmax(zn, fabs(R[IDX(i, c, n)]));
+                    }
+                    znorm_prev[c] = zlast[c];
+                    zlast[c] = zn;
                 }
                 ++iter;
             }
@@ -595,6 +629,7 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
     free(R);
     free(bwd);
     free(znorm_prev);
+    free(zlast);
     return info;
 }
 
@@ -629,9 +664,15 @@ int or_posv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                 or_spotrs(n, 1, W, n, Z, n);
                 for (int i = 0; i < n; ++i) X[IDX(i, c, ldx)] = (double)Z[i] * s;
             }
+            double *zlast = (double *)calloc((size_t)(nrhs > 0 ? nrhs : 1), sizeof(double));
+            for (int c = 0; c < nrhs; ++c) {
+                double xn = 0.0;
+                for (int i = 0; i < n; ++i) xn = fmax(xn, fabs(X[IDX(i, c, ldx)]));
+                zlast[c] = xn;
+            }
             for (;;) {
                 or_dresidual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
-                int done = 1, nonfinite = 0;
+                int done = 1, nonfinite = 0, stalled = 0;
                 for (int c = 0; c < nrhs; ++c) {
                     double rn = 0.0, xn = 0.0, bn = 0.0;
                     for (int i = 0; i < n; ++i) {
@@ -642,12 +683,20 @@ int or_posv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     }
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
-                    if (!(bwd[c] <= tol)) done = 0;
+                    int stagnant = iter >= 2 && zlast[c] > stall_ratio * zprev[c];
+                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    if (!(bwd[c] <= tol && at_floor)) done = 0;
+                    if (!(bwd[c] <= tol) && stagnant) stalled = 1;
                 }
                 if (nonfinite) { flags |= OR_BREAKDOWN; fail = 1; break; }
                 if (done) break;
-                if (iter >= itermax) { fail = 1; break; }
-                int stalled = 0;
+                if (stalled) { flags |= OR_STALLED; fail = 1; break; }
+                if (iter >= itermax) {
+                    int ok = 1;
+                    for (int c = 0; c < nrhs; ++c) if (!(bwd[c] <= tol)) ok = 0;
+                    if (!ok) fail = 1;
+                    break;
+                }
                 for (int c = 0; c < nrhs; ++c) {
                     double rn = 0.0;
                     for (int i = 0; i < n; ++i) rn = fmax(rn, fabs(R[IDX(i, c, n)]));
@@ -660,12 +709,12 @@ int or_posv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                         X[IDX(i, c, ldx)] += z;
                         zn = fmax(zn, fabs(z));
                     }
-                    if (iter >= 1 && zn > stall_ratio * zprev[c] && !(bwd[c] <= tol)) stalled = 1;
-                    zprev[c] = zn;
+                    zprev[c] = zlast[c];
+                    zlast[c] = zn;
                 }
                 ++iter;
-                if (stalled) { flags |= OR_STALLED; fail = 1; break; }
             }
+            free(zlast);
         }
         free(W);
         free(Z);

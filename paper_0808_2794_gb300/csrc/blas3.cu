@@ -1,0 +1,330 @@
+// blas3.cu -- row exchanges, SIMT GEMM update and small triangular solves
+// used inside the blocked factorization (Section 3.1.1: the SGETRF building
+// blocks; Section 2.1: PA = LU).  All matrices are row-major.
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+// ============================================================================
+// Row exchanges.  A run of LAPACK-style swaps (row k <-> row ipiv[k]-1, in
+// order) is first composed into a list of (destination, source) row moves,
+// then every column range is permuted with one gather/scatter through shared
+// memory.  Rows are contiguous in the row-major W, so each move copies whole
+// 128-byte row segments.
+// ============================================================================
+namespace {
+
+constexpr int kComposeThreads = 1024;
+constexpr int kComposeSmemRows = 40960;  // 160 KB map in shared memory
+
+__global__ void __launch_bounds__(kComposeThreads)
+compose_swaps_kernel(const int32_t *__restrict__ ipiv, int k1, int k2, int n, int2 *pairs,
+                     int *npairs, int *gmap) {
+    extern __shared__ int dyn[];
+    const int npiv = k2 - k1;
+    const int rows = n - k1;
+    int *piv = dyn;                       // npiv
+    const bool use_smem = rows <= kComposeSmemRows;
+    int *map = use_smem ? dyn + npiv : gmap + k1;  // map[i - k1] = source row now at row i
+    __shared__ int count;
+    const int tid = threadIdx.x;
+    if (tid == 0) count = 0;
+    for (int t = tid; t < npiv; t += blockDim.x) piv[t] = ipiv[k1 + t] - 1;
+    if (use_smem)
+        for (int t = tid; t < rows; t += blockDim.x) map[t] = k1 + t;
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < npiv; ++t) {
+            const int k = k1 + t, p = piv[t];
+            if (p != k && p >= k && p < n) {
+                const int a = map[k - k1];
+                map[k - k1] = map[p - k1];
+                map[p - k1] = a;
+            }
+        }
+    }
+    __syncthreads();
+    // rows of the block itself
+    for (int t = tid; t < npiv; t += blockDim.x) {
+        const int row = k1 + t;
+        const int src = map[t];
+        if (src != row) {
+            const int slot = atomicAdd(&count, 1);
+            pairs[slot] = make_int2(row, src);
+        }
+    }
+    __syncthreads();
+    // pivot rows below the block (deduplicated through the map itself)
+    for (int t = tid; t < npiv; t += blockDim.x) {
+        const int p = piv[t];
+        if (p >= k2 && p < n) {
+            const int src = atomicExch(&map[p - k1], INT_MIN);
+            if (src != INT_MIN && src != p) {
+                const int slot = atomicAdd(&count, 1);
+                pairs[slot] = make_int2(p, src);
+            }
+        }
+    }
+    __syncthreads();
+    if (!use_smem) {  // restore the identity for the rows we touched
+        for (int t = tid; t < npiv; t += blockDim.x) {
+            map[t] = k1 + t;
+            const int p = piv[t];
+            if (p >= k2 && p < n) map[p - k1] = p;
+        }
+    }
+    if (tid == 0) *npairs = count;
+}
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(256)
+apply_moves_kernel(T *__restrict__ W, long ld, const int2 *__restrict__ pairs,
+                   const int *__restrict__ npairs, int c0, int c1, int c2, int c3) {
+    extern __shared__ unsigned char dyn_raw[];
+    T *tile = reinterpret_cast<T *>(dyn_raw);
+    const int np = *npairs;
+    if (np == 0) return;
+    const int nch1 = (c1 - c0 + CW - 1) / CW;
+    int cs, ce;
+    if ((int)blockIdx.x < nch1) {
+        cs = c0 + blockIdx.x * CW;
+        ce = min(cs + CW, c1);
+    } else {
+        cs = c2 + (blockIdx.x - nch1) * CW;
+        ce = min(cs + CW, c3);
+    }
+    const int w = ce - cs;
+    for (int idx = threadIdx.x; idx < np * CW; idx += blockDim.x) {
+        const int pr = idx / CW, cc = idx - pr * CW;
+        if (cc < w) tile[idx] = W[(long)pairs[pr].y * ld + cs + cc];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < np * CW; idx += blockDim.x) {
+        const int pr = idx / CW, cc = idx - pr * CW;
+        if (cc < w) W[(long)pairs[pr].x * ld + cs + cc] = tile[idx];
+    }
+}
+
+__global__ void apply_moves_vec_kernel(int *v, const int2 *pairs, const int *npairs) {
+    extern __shared__ int vals[];
+    const int np = *npairs;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) vals[t] = v[pairs[t].y];
+    __syncthreads();
+    for (int t = threadIdx.x; t < np; t += blockDim.x) v[pairs[t].x] = vals[t];
+}
+
+}  // namespace
+
+cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int2 *pairs,
+                                 int *npairs, int *map_scratch, cudaStream_t s) {
+    const int npiv = k2 - k1, rows = n - k1;
+    if (npiv <= 0) return cudaSuccess;
+    size_t smem = sizeof(int) * (size_t)npiv;
+    if (rows <= kComposeSmemRows) smem += sizeof(int) * (size_t)rows;
+    cudaError_t e = cudaFuncSetAttribute(compose_swaps_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mp_note_launch();
+    compose_swaps_kernel<<<1, kComposeThreads, smem, s>>>(ipiv, k1, k2, n, pairs, npairs,
+                                                          map_scratch);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
+                               int c0, int c1, int c2, int c3, cudaStream_t s) {
+    constexpr int CW = 128 / sizeof(T);  // 128-byte row segments
+    const int nch = (c1 > c0 ? (c1 - c0 + CW - 1) / CW : 0) + (c3 > c2 ? (c3 - c2 + CW - 1) / CW : 0);
+    if (nch == 0 || max_pairs == 0) return cudaSuccess;
+    if (c1 < c0) c1 = c0;
+    size_t smem = (size_t)max_pairs * CW * sizeof(T);
+    auto kern = apply_moves_kernel<T, CW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mp_note_launch();
+    kern<<<nch, 256, smem, s>>>(W, ld, pairs, npairs, c0, c1, c2, c3);
+    return cudaGetLastError();
+}
+template cudaError_t launch_apply_moves<float>(float *, long, const int2 *, const int *, int, int,
+                                               int, int, int, cudaStream_t);
+template cudaError_t launch_apply_moves<double>(double *, long, const int2 *, const int *, int,
+                                                int, int, int, int, cudaStream_t);
+
+cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
+                                   cudaStream_t s) {
+    if (max_pairs == 0) return cudaSuccess;
+    mp_note_launch();
+    apply_moves_vec_kernel<<<1, 1024, sizeof(int) * (size_t)max_pairs, s>>>(v, pairs, npairs);
+    return cudaGetLastError();
+}
+
+// ============================================================================
+// C[MxN] -= A[MxK] B[KxN] with plain FMA in T (CUDA cores).  Used for the
+// FP32 (and FP64 fallback) updates inside the panel and the triangular
+// solve, and for the all-FP32 trailing update.
+// 256 threads, BM x BN tile, BK-deep slices double-buffered through shared
+// memory; each thread owns a TM x TN block split in two halves so that the
+// shared-memory fragment reads are conflict free.
+// ============================================================================
+namespace {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(256)
+gemm_sub_kernel(int M, int N, int K, const T *__restrict__ A, long lda,
+                const T *__restrict__ B, long ldb, T *__restrict__ C, long ldc) {
+    static_assert((BM / TM) * (BN / TN) == 256, "thread layout");
+    constexpr int TX = BN / TN;          // threads along N
+    constexpr int A_ELEMS = BM * BK / 256;
+    constexpr int B_ELEMS = BK * BN / 256;
+    __shared__ T As[2][BK][BM];
+    __shared__ T Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    // A tile loader: element e of thread -> (row, k)
+    T ra[A_ELEMS], rb[B_ELEMS];
+    auto load_tiles = [&](int k0) {
+#pragma unroll
+        for (int e = 0; e < A_ELEMS; ++e) {
+            const int lin = tid * A_ELEMS + e;      // contiguous along k within a row
+            const int r = lin / BK, kk = lin % BK;
+            const int gr = m0 + r, gk = k0 + kk;
+            ra[e] = (gr < M && gk < K) ? A[(long)gr * lda + gk] : T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < B_ELEMS; ++e) {
+            const int lin = tid * B_ELEMS + e;      // contiguous along n within a k-row
+            const int kk = lin / BN, c = lin % BN;
+            const int gk = k0 + kk, gc = n0 + c;
+            rb[e] = (gk < K && gc < N) ? B[(long)gk * ldb + gc] : T(0);
+        }
+    };
+    auto store_tiles = [&](int buf) {
+#pragma unroll
+        for (int e = 0; e < A_ELEMS; ++e) {
+            const int lin = tid * A_ELEMS + e;
+            As[buf][lin % BK][lin / BK] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < B_ELEMS; ++e) {
+            const int lin = tid * B_ELEMS + e;
+            Bs[buf][lin / BN][lin % BN] = rb[e];
+        }
+    };
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    const int KT = (K + BK - 1) / BK;
+    load_tiles(0);
+    store_tiles(0);
+    __syncthreads();
+    for (int kt = 0; kt < KT; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < KT) load_tiles((kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T af[TM], bf[TN];
+#pragma unroll
+            for (int i = 0; i < TM / 2; ++i) {
+                af[i] = As[cur][kk][ty * (TM / 2) + i];
+                af[i + TM / 2] = As[cur][kk][BM / 2 + ty * (TM / 2) + i];
+            }
+#pragma unroll
+            for (int j = 0; j < TN / 2; ++j) {
+                bf[j] = Bs[cur][kk][tx * (TN / 2) + j];
+                bf[j + TN / 2] = Bs[cur][kk][BN / 2 + tx * (TN / 2) + j];
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+        }
+        if (kt + 1 < KT) store_tiles(cur ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int r = m0 + (i < TM / 2 ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + (i - TM / 2));
+        if (r >= M) continue;
+        T *crow = C + (long)r * ldc;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int c = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + (j - TN / 2));
+            if (c < N) crow[c] -= acc[i][j];
+        }
+    }
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_gemm_sub<float>(int M, int N, int K, const float *A, long lda, const float *B,
+                                   long ldb, float *C, long ldc, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    constexpr int BM = 128, BN = 128, BK = 8;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    mp_note_launch();
+    gemm_sub_kernel<float, BM, BN, BK, 8, 8><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+template <>
+cudaError_t launch_gemm_sub<double>(int M, int N, int K, const double *A, long lda, const double *B,
+                                    long ldb, double *C, long ldc, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    constexpr int BM = 64, BN = 64, BK = 16;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    mp_note_launch();
+    gemm_sub_kernel<double, BM, BN, BK, 4, 4><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+
+// ============================================================================
+// B[m x N] <- L^{-1} B, L unit lower triangular (m <= 64).  One thread per
+// column of B keeps the column in registers; L sits in shared memory.
+// ============================================================================
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+trsm_llnu_small_kernel(int m, int N, const T *__restrict__ L, long ldl, T *__restrict__ B, long ldb) {
+    __shared__ T Ls[64][64];
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+        const int i = idx / 64, l = idx % 64;
+        Ls[i][l] = (i < m && l < i) ? L[(long)i * ldl + l] : T(0);
+    }
+    __syncthreads();
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= N) return;
+    T b[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) b[i] = (i < m) ? B[(long)i * ldb + col] : T(0);
+#pragma unroll
+    for (int i = 1; i < 64; ++i) {
+        T s = b[i];
+#pragma unroll
+        for (int l = 0; l < i; ++l) s = fma(-Ls[i][l], b[l], s);
+        b[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        if (i < m) B[(long)i * ldb + col] = b[i];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_trsm_llnu_small(int m, int N, const T *L, long ldl, T *B, long ldb, cudaStream_t s) {
+    if (m <= 0 || N <= 0) return cudaSuccess;
+    if (m > 64) return cudaErrorInvalidValue;
+    mp_note_launch();
+    trsm_llnu_small_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(m, N, L, ldl, B, ldb);
+    return cudaGetLastError();
+}
+template cudaError_t launch_trsm_llnu_small<float>(int, int, const float *, long, float *, long, cudaStream_t);
+template cudaError_t launch_trsm_llnu_small<double>(int, int, const double *, long, double *, long, cudaStream_t);

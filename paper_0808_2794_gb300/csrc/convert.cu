@@ -1,0 +1,103 @@
+// convert.cu -- W = fl(A) in the working precision with the norms the
+// refinement needs (Section 2.1: "A is converted to single precision for the
+// LU factorization ... the original A is kept"; DLANGE in Table 7).
+//
+// A (FP64, column-major, the caller's) is read once, coalesced, through a
+// 32x32 shared-memory transpose into the row-major W; row sums of |a_ij| are
+// accumulated for ||A||_inf, and any NaN/Inf raises MP_FLAG_NONFINITE_INPUT.
+// Conversion to FP32 is round-to-nearest-even (__double2float_rn).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kColTiles = 8;  // each CTA walks 8 column tiles: fewer row-sum atomics
+
+template <typename Tout>
+__device__ __forceinline__ Tout cvt(double v);
+template <> __device__ __forceinline__ float cvt<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
+
+template <typename Tout>
+__global__ void __launch_bounds__(256)
+convert_transpose_kernel(int n, const double *__restrict__ A, long lda, Tout *__restrict__ W,
+                         long ldw, double *__restrict__ rowsum, MpDevStatus *st) {
+    __shared__ Tout tile[kTile][kTile + 1];
+    __shared__ double rs[8][kTile];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int r0 = blockIdx.x * kTile;
+    double rsum = 0.0;
+    bool bad = false;
+    for (int ct = 0; ct < kColTiles; ++ct) {
+        const int c0 = (blockIdx.y * kColTiles + ct) * kTile;
+        if (c0 >= n) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + ty + 8 * q, r = r0 + tx;
+            double v = 0.0;
+            if (r < n && c < n) v = A[(long)c * lda + r];
+            if (!(fabs(v) <= 1.79769313486231570815e308)) bad = true;
+            rsum += fabs(v);
+            tile[ty + 8 * q][tx] = cvt<Tout>(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + ty + 8 * q, c = c0 + tx;
+            if (r < n && c < n) W[(long)r * ldw + c] = tile[tx][ty + 8 * q];
+        }
+        __syncthreads();
+    }
+    if (bad) mp_flag(st, MP_FLAG_NONFINITE_INPUT);
+    rs[ty][tx] = rsum;
+    __syncthreads();
+    if (ty == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += rs[q][tx];
+        if (r0 + tx < n) atomicAdd(&rowsum[r0 + tx], t);
+    }
+}
+
+__global__ void __launch_bounds__(1024) max_reduce_kernel(int n, const double *__restrict__ v, double *out) {
+    __shared__ double wm[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = v[i];
+        if (x > m || x != x) m = (x != x) ? __longlong_as_double(0x7ff0000000000000LL) : x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wm[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
+}  // namespace
+
+template <typename Tout>
+cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, long ldw,
+                                     double *rowsum, MpDevStatus *st, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dim3 block(32, 8);
+    dim3 grid((n + kTile - 1) / kTile, (n + kTile * kColTiles - 1) / (kTile * kColTiles));
+    mp_note_launch();
+    convert_transpose_kernel<Tout><<<grid, block, 0, s>>>(n, A, lda, W, ldw, rowsum, st);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert_transpose<float>(int, const double *, long, float *, long,
+                                                     double *, MpDevStatus *, cudaStream_t);
+template cudaError_t launch_convert_transpose<double>(int, const double *, long, double *, long,
+                                                      double *, MpDevStatus *, cudaStream_t);
+
+cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s) {
+    mp_note_launch();
+    max_reduce_kernel<<<1, 1024, 0, s>>>(n, v, out);
+    return cudaGetLastError();
+}

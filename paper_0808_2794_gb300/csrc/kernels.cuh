@@ -1,0 +1,81 @@
+// kernels.cuh -- launchers of the device kernels (host-callable, stream-ordered).
+// Every matrix argument here is ROW-major with the given leading dimension
+// unless it is named col-major.
+#pragma once
+
+#include "common.cuh"
+
+// ---- pivoted panel (panel.cu) ----------------------------------------------
+template <typename T> int panel_base_width(int m);
+// LU with partial pivoting of the m x ncols panel starting at P (row-major, ld),
+// ncols <= panel_base_width<T>(m).  ipiv[j] (j < ncols) receives the global
+// 1-based pivot row row0 + p + 1.
+template <typename T>
+cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv,
+                         MpDevStatus *st, cudaStream_t s);
+
+// ---- row exchanges (blas3.cu) ---------------------------------------------
+// Composes the swaps ipiv[k1..k2) (1-based rows) into a list of (dst, src)
+// row moves; npairs_out receives the count (device int).  map_scratch holds
+// n ints (identity on entry, restored on exit) for tall matrices.
+cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int2 *pairs,
+                                 int *npairs, int *map_scratch, cudaStream_t s);
+// Applies the moves to columns [c0,c1) and [c2,c3) of W.
+template <typename T>
+cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
+                               int c0, int c1, int c2, int c3, cudaStream_t s);
+// Applies the moves to an int vector (the running row permutation).
+cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
+                                   cudaStream_t s);
+
+// ---- level-3 helpers (blas3.cu) ---------------------------------------------
+// C[MxN] -= A[MxK] * B[KxN], SIMT FMA in T.
+template <typename T>
+cudaError_t launch_gemm_sub(int M, int N, int K, const T *A, long lda, const T *B, long ldb,
+                            T *C, long ldc, cudaStream_t s);
+// B[m x N] <- L^{-1} B with L unit lower (m x m, ldl), m <= 64.
+template <typename T>
+cudaError_t launch_trsm_llnu_small(int m, int N, const T *L, long ldl, T *B, long ldb,
+                                   cudaStream_t s);
+
+// ---- conversions and norms (convert.cu) -------------------------------------
+// W (row-major, ldw) = (Tout) A (col-major, lda); rowsum[i] += sum_j |a_ij|;
+// non-finite -> flag.  rowsum must be zeroed first.
+template <typename Tout>
+cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, long ldw,
+                                     double *rowsum, MpDevStatus *st, cudaStream_t s);
+cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s);
+
+// ---- triangular solves with the factors (trsv.cu) ---------------------------
+constexpr int TRSV_BS = 64;
+template <typename T>
+cudaError_t launch_diag_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, cudaStream_t s);
+// Lower solve: Y[:,c] = Linv-blocked solve of (P r_c) / s_c, where r is FP64
+// col-major (ldr), perm the row permutation, s_c = 2^ceil(log2 rnorm[c]).
+template <typename T>
+cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv,
+                              const double *R, long ldr, const int *perm, const double *rnorm,
+                              T *Y, long ldy, int *flags, int *ticket, int epoch,
+                              MpDevStatus *st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trsv_upper(int n, int nrhs, const T *W, long ldw, const T *Uinv,
+                              const T *Y, long ldy, T *Z, long ldz, int *flags, int *ticket,
+                              int epoch, MpDevStatus *st, cudaStream_t s);
+
+// ---- FP64 residual and update (refine.cu) -----------------------------------
+int residual_ksplit(int n, int nrhs);
+// part[ks][c][i] partial sums of (A X)[i,c] over column chunk ks.
+cudaError_t launch_residual_partial(int n, int nrhs, const double *A, long lda, const double *X,
+                                    long ldx, double *part, int ksplit, cudaStream_t s);
+// R = B - sum_ks part; rnorm[c] = ||R_c||inf, xnorm[c] = ||X_c||inf (zeroed first).
+cudaError_t launch_residual_finalize(int n, int nrhs, const double *part, int ksplit,
+                                     const double *B, long ldb, const double *X, long ldx,
+                                     double *R, long ldr, double *rnorm, double *xnorm,
+                                     MpDevStatus *st, cudaStream_t s);
+// X[:,c] (+)= s_c * Z[:,c] with s_c = 2^ceil(log2 rnorm[c]); znorm[c] = ||s_c Z_c||inf.
+template <typename T>
+cudaError_t launch_update(int n, int nrhs, const T *Z, long ldz, const double *rnorm, double *X,
+                          long ldx, double *znorm, int assign, cudaStream_t s);
+// bnorm[c] = ||B_c||_inf (zeroed first)
+cudaError_t launch_col_absmax(int n, int nrhs, const double *B, long ldb, double *out,
+                              MpDevStatus *st, cudaStream_t s);

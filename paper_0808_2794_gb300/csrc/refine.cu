@@ -1,0 +1,202 @@
+// refine.cu -- the FP64 steps of the refinement loop (Algorithm 1, steps 4
+// and 7 at eps_d; DGEMM residual and DAXPY update, Section 3.1.1).
+//
+// Residual R = B - A X with the caller's FP64 column-major A: each thread owns
+// one row and walks a chunk of columns (coalesced: a warp reads 256 contiguous
+// bytes of a column), the column chunks are split over CTAs, and the partial
+// sums are added in a fixed order by the finalize kernel (deterministic).
+// The arithmetic is FP64 FMA throughout.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int kRows = 256;   // rows per CTA (one per thread)
+constexpr int kMaxRhs = 8;
+constexpr int kXsElems = 4096;  // 32 KB of x values per CTA
+
+__device__ __forceinline__ double pow2_ceil(double v) {
+    if (!(v > 0.0) || !(v <= 1.79769313486231570815e308)) return 1.0;
+    int e;
+    const double m = frexp(v, &e);
+    return (m == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(kRows)
+residual_partial_kernel(int n, int nrhs, const double *__restrict__ A, long lda,
+                        const double *__restrict__ X, long ldx, double *__restrict__ part,
+                        int chunk) {
+    __shared__ double xsf[kXsElems];  // chunk * NR <= kXsElems
+    const int row = blockIdx.x * kRows + threadIdx.x;
+    const int ks = blockIdx.y;
+    const int c0 = ks * chunk;
+    const int c1 = min(n, c0 + chunk);
+    const int len = max(0, c1 - c0);
+    for (int t = threadIdx.x; t < len * NR; t += blockDim.x) {
+        const int j = t / NR, c = t % NR;
+        xsf[t] = (c < nrhs) ? X[(long)c * ldx + c0 + j] : 0.0;
+    }
+    __syncthreads();
+    if (row >= n) return;
+    double acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+    const double *a = A + (long)c0 * lda + row;
+    int j = 0;
+    for (; j + 4 <= len; j += 4) {
+        const double a0 = __ldcs(a + (long)(j + 0) * lda);
+        const double a1 = __ldcs(a + (long)(j + 1) * lda);
+        const double a2 = __ldcs(a + (long)(j + 2) * lda);
+        const double a3 = __ldcs(a + (long)(j + 3) * lda);
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            acc[c] = fma(a0, xsf[(j + 0) * NR + c], acc[c]);
+            acc[c] = fma(a1, xsf[(j + 1) * NR + c], acc[c]);
+            acc[c] = fma(a2, xsf[(j + 2) * NR + c], acc[c]);
+            acc[c] = fma(a3, xsf[(j + 3) * NR + c], acc[c]);
+        }
+    }
+    for (; j < len; ++j) {
+        const double a0 = a[(long)j * lda];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = fma(a0, xsf[j * NR + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c)
+        if (c < nrhs) part[((long)ks * nrhs + c) * n + row] = acc[c];
+}
+
+__global__ void __launch_bounds__(256)
+residual_finalize_kernel(int n, int nrhs, const double *__restrict__ part, int ksplit,
+                         const double *__restrict__ B, long ldb, const double *__restrict__ X,
+                         long ldx, double *__restrict__ R, long ldr, double *rnorm, double *xnorm,
+                         MpDevStatus *st) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double rv = 0.0, xv = 0.0;
+    if (row < n) {
+        double s = 0.0;
+        for (int ks = 0; ks < ksplit; ++ks) s += part[((long)ks * nrhs + c) * n + row];
+        const double r = B[(long)c * ldb + row] - s;
+        R[(long)c * ldr + row] = r;
+        rv = fabs(r);
+        xv = fabs(X[(long)c * ldx + row]);
+        if (rv != rv) rv = __longlong_as_double(0x7ff0000000000000LL);
+        if (xv != xv) xv = __longlong_as_double(0x7ff0000000000000LL);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rv = fmax(rv, __shfl_xor_sync(0xffffffffu, rv, off));
+        xv = fmax(xv, __shfl_xor_sync(0xffffffffu, xv, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&rnorm[c], rv);
+        atomic_max_nonneg(&xnorm[c], xv);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+update_kernel(int n, const T *__restrict__ Z, long ldz, const double *__restrict__ rnorm,
+              double *__restrict__ X, long ldx, double *znorm, int assign) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double zv = 0.0;
+    if (row < n) {
+        const double s = pow2_ceil(rnorm[c]);
+        const double z = (double)Z[(long)c * ldz + row] * s;
+        double *x = X + (long)c * ldx + row;
+        *x = assign ? z : (*x + z);
+        zv = fabs(z);
+        if (zv != zv) zv = __longlong_as_double(0x7ff0000000000000LL);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) zv = fmax(zv, __shfl_xor_sync(0xffffffffu, zv, off));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&znorm[c], zv);
+}
+
+__global__ void __launch_bounds__(256)
+col_absmax_kernel(int n, const double *__restrict__ B, long ldb, double *out, MpDevStatus *st) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double v = 0.0;
+    if (row < n) {
+        v = fabs(B[(long)c * ldb + row]);
+        if (!(v <= 1.79769313486231570815e308)) {
+            mp_flag(st, MP_FLAG_NONFINITE_INPUT);
+            v = __longlong_as_double(0x7ff0000000000000LL);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&out[c], v);
+}
+
+}  // namespace
+
+static int rhs_pad(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8; }
+
+int residual_ksplit(int n, int nrhs) {
+    const int rowtiles = (n + kRows - 1) / kRows;
+    int ks = (4 * 152 + rowtiles - 1) / rowtiles;  // about four CTAs per SM
+    const int max_by_len = (n + 63) / 64;          // keep chunks >= 64 columns
+    if (ks > max_by_len) ks = max_by_len;
+    if (ks < 1) ks = 1;
+    const int cmax = kXsElems / rhs_pad(nrhs);
+    while ((n + ks - 1) / ks > cmax) ++ks;         // chunk must fit shared memory
+    return ks;
+}
+
+cudaError_t launch_residual_partial(int n, int nrhs, const double *A, long lda, const double *X,
+                                    long ldx, double *part, int ksplit, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
+    const int chunk = (n + ksplit - 1) / ksplit;
+    if (chunk * rhs_pad(nrhs) > kXsElems) return cudaErrorInvalidValue;
+    dim3 grid((n + kRows - 1) / kRows, ksplit);
+    mp_note_launch();
+    if (nrhs <= 1)
+        residual_partial_kernel<1><<<grid, kRows, 0, s>>>(n, nrhs, A, lda, X, ldx, part, chunk);
+    else if (nrhs <= 2)
+        residual_partial_kernel<2><<<grid, kRows, 0, s>>>(n, nrhs, A, lda, X, ldx, part, chunk);
+    else if (nrhs <= 4)
+        residual_partial_kernel<4><<<grid, kRows, 0, s>>>(n, nrhs, A, lda, X, ldx, part, chunk);
+    else
+        residual_partial_kernel<8><<<grid, kRows, 0, s>>>(n, nrhs, A, lda, X, ldx, part, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_finalize(int n, int nrhs, const double *part, int ksplit, const double *B,
+                                     long ldb, const double *X, long ldx, double *R, long ldr,
+                                     double *rnorm, double *xnorm, MpDevStatus *st, cudaStream_t s) {
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    dim3 grid((n + 255) / 256, nrhs);
+    mp_note_launch();
+    residual_finalize_kernel<<<grid, 256, 0, s>>>(n, nrhs, part, ksplit, B, ldb, X, ldx, R, ldr,
+                                                  rnorm, xnorm, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(int n, int nrhs, const T *Z, long ldz, const double *rnorm, double *X,
+                          long ldx, double *znorm, int assign, cudaStream_t s) {
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    dim3 grid((n + 255) / 256, nrhs);
+    mp_note_launch();
+    update_kernel<T><<<grid, 256, 0, s>>>(n, Z, ldz, rnorm, X, ldx, znorm, assign);
+    return cudaGetLastError();
+}
+template cudaError_t launch_update<float>(int, int, const float *, long, const double *, double *, long,
+                                          double *, int, cudaStream_t);
+template cudaError_t launch_update<double>(int, int, const double *, long, const double *, double *,
+                                           long, double *, int, cudaStream_t);
+
+cudaError_t launch_col_absmax(int n, int nrhs, const double *B, long ldb, double *out,
+                              MpDevStatus *st, cudaStream_t s) {
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    dim3 grid((n + 255) / 256, nrhs);
+    mp_note_launch();
+    col_absmax_kernel<<<grid, 256, 0, s>>>(n, B, ldb, out, st);
+    return cudaGetLastError();
+}

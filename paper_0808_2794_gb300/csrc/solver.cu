@@ -1,0 +1,866 @@
+// solver.cu -- host driver of the mixed-precision iterative-refinement solver
+// and the C ABI declared in include/mpsolve.h.
+//
+// Algorithm 1 (Section 2.1):
+//   1: LU <- PA                 low precision: blocked right-looking LU with a
+//                               recursive panel (kernels: panel, row moves,
+//                               triangular solve, trailing update)
+//   2-3: x_0 from L, U          low precision (blocked triangular solves)
+//   do k = 1, 2, ...
+//   4:   r_k = b - A x_{k-1}    FP64 with the caller's FP64 A
+//        check convergence      normwise backward error per column <= tol
+//   5-6: z_k from L, U          low precision, r scaled by a power of two
+//   7:   x_k = x_{k-1} + z_k    FP64
+// Section 4: when refinement cannot converge (breakdown, stall, iteration
+// limit) the solve resorts to a full FP64 LU solve on the GPU.
+//
+// Every step runs in a CUDA kernel on the caller's stream; the host only
+// reads back a small status block once per iteration to decide whether to
+// continue.  All scratch memory comes from the caller's workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512];
+
+int mp_cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_err, sizeof g_err, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return -1000 - (int)e;
+}
+int mp_arg_fail(int idx, const char *msg) {
+    snprintf(g_err, sizeof g_err, "argument %d: %s", idx, msg);
+    return -idx;
+}
+void mp_set_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+extern "C" const char *mp_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------
+// instrumentation: launch counter and per-class event timing
+// ---------------------------------------------------------------------------
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+static std::atomic<long long> g_launches{0};
+void mp_note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+extern "C" long long mp_launch_count(void) { return g_launches.load(); }
+
+namespace {
+struct ProfRec {
+    int cls;
+    double work;
+    cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+unsigned g_prof_mask = 0;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+MpProfScope::MpProfScope(int cls_, double work_, cudaStream_t s_) : cls(cls_), work(work_), s(s_) {
+    if (g_prof_mask & (1u << cls)) {
+        if (cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+        else e0 = nullptr;
+    }
+}
+MpProfScope::~MpProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.push_back({cls, work, e0, e1});
+}
+
+extern "C" void mp_profile_enable(unsigned mask) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    for (auto &r : g_prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    g_prof.clear();
+    g_prof_mask = mask;
+}
+
+extern "C" int mp_profile_collect(double *ms, long long *launches, double *work) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    for (int c = 0; c < MP_KC_COUNT; ++c) { ms[c] = 0; launches[c] = 0; work[c] = 0; }
+    for (auto &r : g_prof) {
+        MP_CUDA_TRY(cudaEventSynchronize(r.e1));
+        float t = 0;
+        MP_CUDA_TRY(cudaEventElapsedTime(&t, r.e0, r.e1));
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+        work[r.cls] += r.work;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    g_prof.clear();
+    return 0;
+}
+
+extern "C" void mp_default_opts(mp_opts *o) {
+    o->prec = MP_PREC_FP32;
+    o->refine = MP_REFINE_CLASSICAL;
+    o->itermax = 30;
+    o->tol = 1e-14;
+    o->gmres_restart = 30;
+    o->gmres_tol = 1e-6;
+    o->stall_ratio = 0.5;
+    o->allow_fallback = 1;
+    o->nb_outer = 0;
+    o->nb_inner = 0;
+}
+
+extern "C" int mp_factor_ld(int n) { return std::max(32, (n + 31) / 32 * 32); }
+
+namespace {
+
+constexpr int kMaxRhs = 8;
+
+// Status block in device memory, read back by the host once per iteration.
+struct StatusBlock {
+    MpDevStatus st;
+    double pad0;
+    double bnorm[kMaxRhs];
+    double rnorm[kMaxRhs];
+    double xnorm[kMaxRhs];
+    double znorm[kMaxRhs];
+};
+
+int outer_nb(int n, const mp_opts &o) {
+    if (o.nb_outer > 0) return std::max(32, o.nb_outer / 32 * 32);
+    if (o.prec == MP_PREC_FP32) return n >= 4096 ? 256 : 128;
+    return n >= 8192 ? 512 : 256;
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, flagsL, flagsU,
+        tickets, R, Y, Z, part, tc, total;
+    size_t W_bytes;
+    int ldw, nblk, ksplit, nb;
+};
+
+size_t carve(size_t &off, size_t bytes) {
+    off = align_up(off, 256);
+    const size_t at = off;
+    off += bytes;
+    return at;
+}
+
+// fp64_space: room for the FP64 fallback (W, inverses, vectors sized for double)
+Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
+    Layout L{};
+    L.ldw = mp_factor_ld(n);
+    L.nblk = (n + TRSV_BS - 1) / TRSV_BS;
+    L.ksplit = residual_ksplit(n, nrhs);
+    L.nb = outer_nb(n, o);
+    const size_t el = fp64_space ? sizeof(double) : sizeof(float);
+    const int rhs = std::max(nrhs, 1);
+    size_t off = 0;
+    L.status = carve(off, sizeof(StatusBlock));
+    L.rowsum = carve(off, sizeof(double) * (size_t)n);
+    L.W_bytes = (size_t)n * (size_t)L.ldw * el;
+    L.W = carve(off, L.W_bytes);
+    L.perm = carve(off, sizeof(int) * (size_t)n);
+    L.ipiv = carve(off, sizeof(int) * (size_t)n);
+    L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, L.nb));
+    L.npairs = carve(off, sizeof(int) * 4);
+    L.map = carve(off, sizeof(int) * (size_t)n);
+    L.Linv = carve(off, el * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    L.Uinv = carve(off, el * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.tickets = carve(off, sizeof(int) * 4);
+    L.R = carve(off, sizeof(double) * (size_t)n * rhs);
+    L.Y = carve(off, el * (size_t)n * rhs);
+    L.Z = carve(off, el * (size_t)n * rhs);
+    L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
+    L.tc = carve(off, tc_workspace_bytes(n, L.nb, o.prec));
+    L.total = align_up(off, 256);
+    return L;
+}
+
+template <typename P>
+P *at(void *work, size_t off) {
+    return reinterpret_cast<P *>(static_cast<char *>(work) + off);
+}
+
+__global__ void iota_kernel(int *v, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+cudaError_t launch_iota(int *v, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    mp_note_launch();
+    mp_note_launch();
+    iota_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, s>>>(v, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// factorization
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FactorCtx {
+    T *W;
+    long ld;
+    int n;
+    int32_t *ipiv;
+    int *perm;
+    int2 *pairs;
+    int *npairs;
+    int *map;
+    MpDevStatus *st;
+    cudaStream_t s;
+    int prec;
+    void *tc;
+};
+
+#define CU(expr)                                      \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return _e;             \
+    } while (0)
+
+// B <- L^{-1} B, L unit lower m x m (recursive: small base solve + GEMM update).
+template <typename T>
+cudaError_t trsm_rec(int m, int N, const T *L, long ldl, T *B, long ldb, cudaStream_t s) {
+    if (m <= 0 || N <= 0) return cudaSuccess;
+    if (m <= 64) return launch_trsm_llnu_small<T>(m, N, L, ldl, B, ldb, s);
+    const int m1 = (m / 2 + 31) / 32 * 32;
+    CU(trsm_rec<T>(m1, N, L, ldl, B, ldb, s));
+    CU(launch_gemm_sub<T>(m - m1, N, m1, L + (long)m1 * ldl, ldl, B, ldb, B + (long)m1 * ldb, ldb, s));
+    return trsm_rec<T>(m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb, s);
+}
+
+// Applies the swaps ipiv[k1..k2) to columns [c0,c1) and [c2,c3).
+template <typename T>
+cudaError_t row_moves(FactorCtx<T> &c, int k1, int k2, int c0, int c1, int c2, int c3, bool perm) {
+    MpProfScope ps(MP_KC_ROWMOVES, 4.0 * (k2 - k1) * ((c1 - c0) + (c3 - c2)) * sizeof(T), c.s);
+    CU(launch_compose_swaps(c.ipiv, k1, k2, c.n, c.pairs, c.npairs, c.map, c.s));
+    CU(launch_apply_moves<T>(c.W, c.ld, c.pairs, c.npairs, 2 * (k2 - k1), c0, c1, c2, c3, c.s));
+    if (perm) CU(launch_apply_moves_vec(c.perm, c.pairs, c.npairs, 2 * (k2 - k1), c.s));
+    return cudaSuccess;
+}
+
+// Recursive LU of the columns [k0, k0+ncols) of rows [k0, n): left half,
+// update of the right half (row moves, triangular solve, FP32 GEMM), right
+// half, then the right half's row moves applied to the left half.
+template <typename T>
+cudaError_t getrf_rec(FactorCtx<T> &c, int k0, int ncols) {
+    const int m = c.n - k0;
+    const int nb = panel_base_width<T>(m);
+    T *W = c.W;
+    const long ld = c.ld;
+    if (ncols <= nb) {
+        MpProfScope ps(MP_KC_PANEL, (double)m * ncols * ncols - (double)ncols * ncols * ncols / 3.0, c.s);
+        return launch_panel<T>(W + (long)k0 * ld + k0, ld, m, ncols, k0, c.ipiv + k0, c.st, c.s);
+    }
+    int n1 = (ncols / 2) / nb * nb;
+    if (n1 < nb) n1 = nb;
+    CU(getrf_rec<T>(c, k0, n1));
+    CU(row_moves<T>(c, k0, k0 + n1, k0 + n1, k0 + ncols, 0, 0, false));
+    {
+        MpProfScope ps(MP_KC_PANELGEMM, (double)n1 * n1 * (ncols - n1) + 2.0 * (m - n1) * (ncols - n1) * n1, c.s);
+        CU(trsm_rec<T>(n1, ncols - n1, W + (long)k0 * ld + k0, ld, W + (long)k0 * ld + k0 + n1, ld, c.s));
+        CU(launch_gemm_sub<T>(m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
+                              W + (long)k0 * ld + k0 + n1, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld, c.s));
+    }
+    CU(getrf_rec<T>(c, k0 + n1, ncols - n1));
+    return row_moves<T>(c, k0 + n1, k0 + ncols, k0, k0 + n1, 0, 0, false);
+}
+
+// Blocked right-looking LU: panel of width nb (recursive), row moves on the
+// rest of the matrix, U12 = L11^{-1} A12, A22 -= L21 U12 at precision prec.
+template <typename T>
+cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
+    const int n = c.n;
+    T *W = c.W;
+    const long ld = c.ld;
+    for (int k = 0; k < n; k += nb) {
+        const int nbk = std::min(nb, n - k);
+        CU(getrf_rec<T>(c, k, nbk));
+        CU(row_moves<T>(c, k, k + nbk, 0, k, k + nbk, n, true));
+        const int rest = n - k - nbk;
+        if (rest > 0) {
+            {
+                MpProfScope ps(MP_KC_TRSM, (double)nbk * nbk * rest, c.s);
+                CU(trsm_rec<T>(nbk, rest, W + (long)k * ld + k, ld, W + (long)k * ld + k + nbk, ld, c.s));
+            }
+            MpProfScope ps(MP_KC_UPDATE, 2.0 * rest * rest * nbk, c.s);
+            const T *L21 = W + (long)(k + nbk) * ld + k;
+            const T *U12 = W + (long)k * ld + k + nbk;
+            T *A22 = W + (long)(k + nbk) * ld + k + nbk;
+            if (sizeof(T) == 4 && c.prec != MP_PREC_FP32) {
+                CU(tc_trailing_update(c.prec, rest, rest, nbk, reinterpret_cast<const float *>(L21), ld,
+                                      reinterpret_cast<const float *>(U12), ld,
+                                      reinterpret_cast<float *>(A22), ld, c.tc, c.st, c.s));
+            } else {
+                CU(launch_gemm_sub<T>(rest, rest, nbk, L21, ld, U12, ld, A22, ld, c.s));
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// the solve
+// ---------------------------------------------------------------------------
+struct Solve {
+    int n, nrhs;
+    const double *A;
+    int lda;
+    const double *B;
+    int ldb;
+    double *X;
+    int ldx;
+    void *work;
+    Layout L;
+    cudaStream_t s;
+    StatusBlock *sb;
+    int epoch;
+};
+
+int read_status(Solve &S, StatusBlock &h) {
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, S.sb, sizeof(StatusBlock), cudaMemcpyDeviceToHost, S.s));
+    MP_CUDA_TRY(cudaStreamSynchronize(S.s));
+    return 0;
+}
+
+// z = U^{-1} L^{-1} P (r / s) in T, from the FP64 R (rnorm gives s); result in S.Z.
+template <typename T>
+int lowp_solve(Solve &S, const double *R, long ldr, const double *rnorm) {
+    const Layout &L = S.L;
+    T *W = at<T>(S.work, L.W);
+    ++S.epoch;
+    MpProfScope ps(MP_KC_TRSV, (double)S.n * S.n * sizeof(T) + 4.0 * S.n * S.nrhs * sizeof(T), S.s);
+    MP_CUDA_TRY(launch_trsv_lower<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Linv), R, ldr,
+                                     at<int>(S.work, L.perm), rnorm, at<T>(S.work, L.Y), S.n,
+                                     at<int>(S.work, L.flagsL), at<int>(S.work, L.tickets), S.epoch,
+                                     &S.sb->st, S.s));
+    MP_CUDA_TRY(launch_trsv_upper<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Uinv), at<T>(S.work, L.Y),
+                                     S.n, at<T>(S.work, L.Z), S.n, at<int>(S.work, L.flagsU),
+                                     at<int>(S.work, L.tickets) + 1, S.epoch, &S.sb->st, S.s));
+    return 0;
+}
+
+int residual(Solve &S) {
+    const Layout &L = S.L;
+    MP_CUDA_TRY(cudaMemsetAsync(S.sb->rnorm, 0, sizeof(double) * 2 * kMaxRhs, S.s));  // rnorm, xnorm
+    MpProfScope ps(MP_KC_RESIDUAL, 8.0 * S.n * S.n + 32.0 * S.n * S.nrhs, S.s);
+    MP_CUDA_TRY(launch_residual_partial(S.n, S.nrhs, S.A, S.lda, S.X, S.ldx, at<double>(S.work, L.part),
+                                        L.ksplit, S.s));
+    MP_CUDA_TRY(launch_residual_finalize(S.n, S.nrhs, at<double>(S.work, L.part), L.ksplit, S.B, S.ldb,
+                                         S.X, S.ldx, at<double>(S.work, L.R), S.n, S.sb->rnorm,
+                                         S.sb->xnorm, &S.sb->st, S.s));
+    return 0;
+}
+
+// Resets the per-solve flags/tickets (epoch restarts at 0).
+int reset_sync(Solve &S) {
+    const Layout &L = S.L;
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsL), 0, sizeof(int) * L.nblk, S.s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsU), 0, sizeof(int) * L.nblk, S.s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.tickets), 0, sizeof(int) * 4, S.s));
+    S.epoch = 0;
+    return 0;
+}
+
+// Factor (T = float: low precision; T = double: fallback) and leave factors,
+// perm and diagonal inverses in the workspace.  Returns the zero-pivot info.
+template <typename T>
+int factor(Solve &S, int prec, int nb, int *info_out, uint32_t *flags_out) {
+    const Layout &L = S.L;
+    T *W = at<T>(S.work, L.W);
+    MP_CUDA_TRY(launch_iota(at<int>(S.work, L.perm), S.n, S.s));
+    MP_CUDA_TRY(launch_iota(at<int>(S.work, L.map), S.n, S.s));
+    FactorCtx<T> c{W, (long)L.ldw, S.n, at<int32_t>(S.work, L.ipiv), at<int>(S.work, L.perm),
+                   at<int2>(S.work, L.pairs), at<int>(S.work, L.npairs), at<int>(S.work, L.map),
+                   &S.sb->st, S.s, prec, at<void>(S.work, L.tc)};
+    MP_CUDA_TRY(getrf_blocked<T>(c, nb));
+    MP_CUDA_TRY(launch_diag_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv), S.s));
+    StatusBlock h;
+    int e = read_status(S, h);
+    if (e) return e;
+    *info_out = h.st.zero_pivot;
+    *flags_out = h.st.flags;
+    return 0;
+}
+
+double bwd_of(const StatusBlock &h, int c) {
+    const double den = h.st.anorm * h.xnorm[c] + h.bnorm[c];
+    if (!(h.rnorm[c] == h.rnorm[c])) return INFINITY;
+    return den > 0.0 ? h.rnorm[c] / den : (h.rnorm[c] > 0.0 ? INFINITY : 0.0);
+}
+
+// Refinement loop with the factors of precision T (Algorithm 1 steps 2-7).
+// x_k is accepted when every column has bwd <= tol AND has reached the FP64
+// floor (bwd == 0, last correction <= 4 u64 ||x_k||, or the corrections
+// stopped shrinking); the shrink test with bwd > tol is a stall.
+// Returns 0, or a CUDA error code; *conv tells whether all columns converged.
+template <typename T>
+int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *st, bool *conv,
+           int *iters, uint32_t *flags) {
+    StatusBlock h;
+    // steps 2-3: x_0 from b (scaled by 2^ceil(log2 ||b||)); znorm = ||x_0||
+    MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
+    int e = lowp_solve<T>(S, S.B, S.ldb, S.sb->bnorm);
+    if (e) return e;
+    MP_CUDA_TRY(launch_update<T>(S.n, S.nrhs, at<T>(S.work, S.L.Z), S.n, S.sb->bnorm, S.X, S.ldx,
+                                 S.sb->znorm, 1, S.s));
+    double zprev[kMaxRhs] = {0};
+    int it = 0;
+    *conv = false;
+    const double u64 = 1.1102230246251565e-16;
+    for (;;) {
+        if ((e = residual(S))) return e;
+        if ((e = read_status(S, h))) return e;
+        double worst = 0.0;
+        bool done = true, nonfinite = false, stalled = false, all_tol = true;
+        for (int c = 0; c < S.nrhs; ++c) {
+            const double b = bwd_of(h, c);
+            const bool stagnant = it >= 2 && h.znorm[c] > o.stall_ratio * zprev[c];
+            const bool at_floor = b == 0.0 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant;
+            if (!(b <= o.tol)) all_tol = false;
+            if (!(b <= o.tol && at_floor)) done = false;
+            if (!(b <= o.tol) && stagnant) stalled = true;
+            if (!(b == b) || std::isinf(b)) nonfinite = true;
+            worst = std::max(worst, std::isnan(b) ? INFINITY : b);
+        }
+        if (st) {
+            if (st->nhist < 32) st->hist[st->nhist++] = worst;
+            st->bwd_err = worst;
+        }
+        *flags |= h.st.flags & (MP_FLAG_TIMEOUT | MP_FLAG_NONFINITE_INPUT);
+        if (h.st.flags & MP_FLAG_TIMEOUT) break;
+        if (nonfinite) { *flags |= MP_FLAG_LOWP_BREAKDOWN; break; }
+        if (done) { *conv = true; break; }
+        if (stalled && stall_test) { *flags |= MP_FLAG_STALLED; break; }
+        if (it >= itermax) { *conv = all_tol; break; }
+        std::memcpy(zprev, h.znorm, sizeof zprev);
+        // steps 5-7
+        if ((e = lowp_solve<T>(S, at<double>(S.work, S.L.R), S.n, S.sb->rnorm))) return e;
+        MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
+        MP_CUDA_TRY(launch_update<T>(S.n, S.nrhs, at<T>(S.work, S.L.Z), S.n, S.sb->rnorm, S.X, S.ldx,
+                                     S.sb->znorm, 0, S.s));
+        if (st) st->n_precond += 1;
+        ++it;
+    }
+    *iters = it;
+    return 0;
+}
+
+int validate_opts(const mp_opts &o) {
+    if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_FP16) return 1;
+    if (o.itermax < 0 || !(o.tol > 0.0) || o.stall_ratio <= 0.0) return 1;
+    return 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" size_t mp_gesv_workspace_bytes(int n, int nrhs, const mp_opts *opts) {
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0 || nrhs < 0) return 0;
+    return make_layout(n, nrhs, o, o.allow_fallback != 0).total;
+}
+
+extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
+                       double *dX, int ldx, int32_t *dipiv, void *work, size_t work_bytes,
+                       const mp_opts *opts, mp_stats *stats, void *stream) {
+    g_err[0] = 0;
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 65536) return mp_arg_fail(1, "n > 65536 is not supported");
+    if (n > 0 && !dA) return mp_arg_fail(3, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(4, "lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dB) return mp_arg_fail(5, "B is NULL");
+    if (ldb < std::max(1, n)) return mp_arg_fail(6, "ldb < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dX) return mp_arg_fail(7, "X is NULL");
+    if (ldx < std::max(1, n)) return mp_arg_fail(8, "ldx < max(1, n)");
+    if (n > 0 && !dipiv) return mp_arg_fail(9, "ipiv is NULL");
+    if (validate_opts(o)) return mp_arg_fail(12, "invalid options");
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+    }
+    if (n == 0 || nrhs == 0) return 0;
+    const bool fb = o.allow_fallback != 0;
+    Layout L = make_layout(n, nrhs, o, fb);
+    if (!work) return mp_arg_fail(10, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(11, "workspace too small");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Solve S{n, nrhs, dA, lda, dB, ldb, dX, ldx, work, L, s, at<StatusBlock>(work, L.status), 0};
+    cudaEvent_t ev[5] = {};
+    const bool timing = stats != nullptr;
+    if (timing)
+        for (auto &e : ev) MP_CUDA_TRY(cudaEventCreate(&e));
+    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+
+    mark(0);
+    MP_CUDA_TRY(cudaMemsetAsync(S.sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<double>(work, L.rowsum), 0, sizeof(double) * n, s));
+    if (reset_sync(S)) return -1000;
+    MP_CUDA_TRY(launch_convert_transpose<float>(n, dA, lda, at<float>(work, L.W), L.ldw,
+                                                at<double>(work, L.rowsum), &S.sb->st, s));
+    MP_CUDA_TRY(launch_max_reduce(n, at<double>(work, L.rowsum), &S.sb->st.anorm, s));
+    MP_CUDA_TRY(launch_col_absmax(n, nrhs, dB, ldb, S.sb->bnorm, &S.sb->st, s));
+    mark(1);
+
+    uint32_t flags = 0;
+    int info = 0, iters = 0, e;
+    bool conv = false;
+    uint32_t fflags = 0;
+    if ((e = factor<float>(S, o.prec, L.nb, &info, &fflags))) return e;
+    mark(2);
+    flags |= fflags & (MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT);
+    if (!(flags & (MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT))) {
+        if ((e = refine<float>(S, o, o.itermax, true, stats, &conv, &iters, &flags))) return e;
+    }
+    if (stats) stats->info = info;
+    mark(3);
+    int ret = 0;
+    if (!conv && fb && !(flags & MP_FLAG_NONFINITE_INPUT)) {
+        // Section 4: resort to the double-precision solver (FP64 LU on the GPU)
+        Layout L64 = L;
+        S.L = L64;
+        MP_CUDA_TRY(cudaMemsetAsync(&S.sb->st.zero_pivot, 0, sizeof(int), s));
+        MP_CUDA_TRY(cudaMemsetAsync(&S.sb->st.flags, 0, sizeof(uint32_t), s));
+        if (reset_sync(S)) return -1000;
+        MP_CUDA_TRY(launch_convert_transpose<double>(n, dA, lda, at<double>(work, L.W), L.ldw,
+                                                     at<double>(work, L.rowsum), &S.sb->st, s));
+        int info64 = 0;
+        uint32_t f64 = 0;
+        if ((e = factor<double>(S, MP_PREC_FP32, std::min(L.nb, 256), &info64, &f64))) return e;
+        flags |= MP_FLAG_FALLBACK;
+        if (info64 > 0) {
+            ret = info64;
+        } else {
+            bool conv64 = false;
+            int it64 = 0;
+            uint32_t fl64 = 0;
+            if ((e = refine<double>(S, o, 5, false, nullptr, &conv64, &it64, &fl64))) return e;
+            flags |= fl64 & MP_FLAG_TIMEOUT;
+            StatusBlock h;
+            if ((e = read_status(S, h))) return e;
+            double worst = 0.0;
+            for (int c = 0; c < nrhs; ++c) worst = std::max(worst, bwd_of(h, c));
+            if (stats) stats->bwd_err = worst;
+        }
+        iters = -1;
+    } else if (!conv) {
+        flags |= MP_FLAG_NOT_CONVERGED;
+    }
+    MP_CUDA_TRY(cudaMemcpyAsync(dipiv, at<int32_t>(work, L.ipiv), sizeof(int32_t) * n,
+                                cudaMemcpyDeviceToDevice, s));
+    mark(4);
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iter = iters;
+        stats->flags = flags;
+        if (timing) {
+            cudaEventElapsedTime(&stats->ms_convert, ev[0], ev[1]);
+            cudaEventElapsedTime(&stats->ms_factor, ev[1], ev[2]);
+            cudaEventElapsedTime(&stats->ms_refine, ev[2], ev[3]);
+            cudaEventElapsedTime(&stats->ms_fallback, ev[3], ev[4]);
+        }
+    }
+    if (timing)
+        for (auto &ev_ : ev) cudaEventDestroy(ev_);
+    return ret;
+}
+
+extern "C" size_t mp_gesv_host_workspace_bytes(int n, int nrhs, const mp_opts *opts) {
+    if (n < 0 || nrhs < 0) return 0;
+    size_t off = 0;
+    carve(off, sizeof(double) * (size_t)n * n);
+    carve(off, sizeof(double) * (size_t)n * std::max(nrhs, 1));
+    carve(off, sizeof(double) * (size_t)n * std::max(nrhs, 1));
+    carve(off, sizeof(int32_t) * (size_t)std::max(n, 1));
+    off = align_up(off, 256);
+    return off + mp_gesv_workspace_bytes(n, nrhs, opts);
+}
+
+extern "C" int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const double *hB, int ldb,
+                            double *hX, int ldx, int32_t *hipiv, void *work, size_t work_bytes,
+                            const mp_opts *opts, mp_stats *stats, void *stream) {
+    g_err[0] = 0;
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 0 && !hA) return mp_arg_fail(3, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(4, "lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && !hB) return mp_arg_fail(5, "B is NULL");
+    if (ldb < std::max(1, n)) return mp_arg_fail(6, "ldb < max(1, n)");
+    if (n > 0 && nrhs > 0 && !hX) return mp_arg_fail(7, "X is NULL");
+    if (ldx < std::max(1, n)) return mp_arg_fail(8, "ldx < max(1, n)");
+    if (n > 0 && !hipiv) return mp_arg_fail(9, "ipiv is NULL");
+    if (n == 0 || nrhs == 0) return 0;
+    if (!work) return mp_arg_fail(10, "workspace is NULL");
+    if (work_bytes < mp_gesv_host_workspace_bytes(n, nrhs, opts)) return mp_arg_fail(11, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t off = 0;
+    double *dA = at<double>(work, carve(off, sizeof(double) * (size_t)n * n));
+    double *dB = at<double>(work, carve(off, sizeof(double) * (size_t)n * nrhs));
+    double *dX = at<double>(work, carve(off, sizeof(double) * (size_t)n * nrhs));
+    int32_t *dp = at<int32_t>(work, carve(off, sizeof(int32_t) * (size_t)n));
+    off = align_up(off, 256);
+    MP_CUDA_TRY(cudaMemcpy2DAsync(dA, sizeof(double) * n, hA, sizeof(double) * lda, sizeof(double) * n, n,
+                                  cudaMemcpyHostToDevice, s));
+    MP_CUDA_TRY(cudaMemcpy2DAsync(dB, sizeof(double) * n, hB, sizeof(double) * ldb, sizeof(double) * n,
+                                  nrhs, cudaMemcpyHostToDevice, s));
+    int r = mp_gesv(n, nrhs, dA, n, dB, n, dX, n, dp, static_cast<char *>(work) + off, work_bytes - off,
+                    opts, stats, stream);
+    if (r < 0 && r > -1000) return r;  // argument errors are not expected here
+    MP_CUDA_TRY(cudaMemcpy2DAsync(hX, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n,
+                                  nrhs, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaMemcpyAsync(hipiv, dp, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// step entry points
+// ---------------------------------------------------------------------------
+namespace {
+struct StepLayout {
+    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, flagsL, flagsU, tickets, Y, Z, part,
+        tc, total;
+    int nblk, ksplit;
+};
+StepLayout step_layout(int n, int nrhs, int nb, int prec) {
+    StepLayout L{};
+    L.nblk = (n + TRSV_BS - 1) / TRSV_BS;
+    L.ksplit = residual_ksplit(std::max(n, 1), std::max(nrhs, 1));
+    const int rhs = std::max(nrhs, 1);
+    size_t off = 0;
+    L.status = carve(off, sizeof(StatusBlock));
+    L.rowsum = carve(off, sizeof(double) * (size_t)n);
+    L.perm = carve(off, sizeof(int) * (size_t)n);
+    L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, nb));
+    L.npairs = carve(off, sizeof(int) * 4);
+    L.map = carve(off, sizeof(int) * (size_t)n);
+    L.Linv = carve(off, sizeof(float) * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    L.Uinv = carve(off, sizeof(float) * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.tickets = carve(off, sizeof(int) * 4);
+    L.Y = carve(off, sizeof(float) * (size_t)n * rhs);
+    L.Z = carve(off, sizeof(float) * (size_t)n * rhs);
+    L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
+    L.tc = carve(off, tc_workspace_bytes(n, nb, prec));
+    L.total = align_up(off, 256);
+    return L;
+}
+}  // namespace
+
+extern "C" size_t mp_getrf_workspace_bytes(int n, const mp_opts *opts) {
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0) return 0;
+    return step_layout(n, 1, outer_nb(n, o), o.prec).total;
+}
+extern "C" size_t mp_getrs_workspace_bytes(int n, int nrhs) {
+    if (n < 0 || nrhs < 0) return 0;
+    return step_layout(n, nrhs, 32, MP_PREC_FP32).total;
+}
+extern "C" size_t mp_residual_workspace_bytes(int n, int nrhs) {
+    if (n < 0 || nrhs < 0) return 0;
+    return step_layout(n, nrhs, 32, MP_PREC_FP32).total;
+}
+
+extern "C" int mp_convert(int n, const double *dA, int lda, float *dW, int ldw, double *d_anorm,
+                          uint32_t *d_flags, void *work, size_t work_bytes, void *stream) {
+    g_err[0] = 0;
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (n > 0 && !dA) return mp_arg_fail(2, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(3, "lda < max(1, n)");
+    if (n > 0 && !dW) return mp_arg_fail(4, "W is NULL");
+    if (ldw < std::max(1, n)) return mp_arg_fail(5, "ldw < max(1, n)");
+    if (!d_anorm) return mp_arg_fail(6, "anorm is NULL");
+    if (!d_flags) return mp_arg_fail(7, "flags is NULL");
+    StepLayout L = step_layout(n, 1, 32, MP_PREC_FP32);
+    if (!work) return mp_arg_fail(8, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(9, "workspace too small");
+    if (n == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = at<StatusBlock>(work, L.status);
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<double>(work, L.rowsum), 0, sizeof(double) * n, s));
+    MP_CUDA_TRY(launch_convert_transpose<float>(n, dA, lda, dW, ldw, at<double>(work, L.rowsum), &sb->st, s));
+    MP_CUDA_TRY(launch_max_reduce(n, at<double>(work, L.rowsum), d_anorm, s));
+    MP_CUDA_TRY(cudaMemcpyAsync(d_flags, &sb->st.flags, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    return 0;
+}
+
+extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp_opts *opts, void *work,
+                             size_t work_bytes, int *info, uint32_t *flags, void *stream) {
+    g_err[0] = 0;
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0 || n > 65536) return mp_arg_fail(1, "n out of range [0, 65536]");
+    if (n > 0 && !dW) return mp_arg_fail(2, "W is NULL");
+    if (ldw < mp_factor_ld(n) || ldw % 32) return mp_arg_fail(3, "ldw must be a multiple of 32 >= n");
+    if (n > 0 && !dipiv) return mp_arg_fail(4, "ipiv is NULL");
+    if (validate_opts(o)) return mp_arg_fail(5, "invalid options");
+    const int nb = outer_nb(n, o);
+    StepLayout L = step_layout(n, 1, nb, o.prec);
+    if (!work) return mp_arg_fail(6, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(7, "workspace too small");
+    if (info) *info = 0;
+    if (flags) *flags = 0;
+    if (n == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = at<StatusBlock>(work, L.status);
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(launch_iota(at<int>(work, L.perm), n, s));
+    MP_CUDA_TRY(launch_iota(at<int>(work, L.map), n, s));
+    FactorCtx<float> c{dW, (long)ldw, n, dipiv, at<int>(work, L.perm), at<int2>(work, L.pairs),
+                       at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc)};
+    MP_CUDA_TRY(getrf_blocked<float>(c, nb));
+    StatusBlock h;
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (info) *info = h.st.zero_pivot;
+    if (flags) *flags = h.st.flags;
+    return 0;
+}
+
+extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const int32_t *dipiv,
+                             const double *dR, int ldr, double *dZ, int ldz, void *work,
+                             size_t work_bytes, void *stream) {
+    g_err[0] = 0;
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 0 && !dW) return mp_arg_fail(3, "W is NULL");
+    if (ldw < std::max(1, n)) return mp_arg_fail(4, "ldw < max(1, n)");
+    if (n > 0 && !dipiv) return mp_arg_fail(5, "ipiv is NULL");
+    if (n > 0 && nrhs > 0 && !dR) return mp_arg_fail(6, "R is NULL");
+    if (ldr < std::max(1, n)) return mp_arg_fail(7, "ldr < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dZ) return mp_arg_fail(8, "Z is NULL");
+    if (ldz < std::max(1, n)) return mp_arg_fail(9, "ldz < max(1, n)");
+    StepLayout L = step_layout(n, nrhs, 32, MP_PREC_FP32);
+    if (!work) return mp_arg_fail(10, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(11, "workspace too small");
+    if (n == 0 || nrhs == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = at<StatusBlock>(work, L.status);
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsL), 0, sizeof(int) * L.nblk, s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsU), 0, sizeof(int) * L.nblk, s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.tickets), 0, sizeof(int) * 4, s));
+    // row permutation from the pivots: compose all n swaps, apply to identity
+    int *perm = at<int>(work, L.perm);
+    MP_CUDA_TRY(launch_iota(perm, n, s));
+    MP_CUDA_TRY(launch_iota(at<int>(work, L.map), n, s));
+    const int chunk = 4096;  // compose in chunks (bounded shared memory for the pivot copy)
+    for (int k = 0; k < n; k += chunk) {
+        const int k2 = std::min(n, k + chunk);
+        MP_CUDA_TRY(launch_compose_swaps(dipiv, k, k2, n, at<int2>(work, L.pairs), at<int>(work, L.npairs),
+                                         at<int>(work, L.map), s));
+        MP_CUDA_TRY(launch_apply_moves_vec(perm, at<int2>(work, L.pairs), at<int>(work, L.npairs),
+                                           2 * (k2 - k), s));
+    }
+    MP_CUDA_TRY(launch_diag_inverses<float>(n, dW, ldw, at<float>(work, L.Linv), at<float>(work, L.Uinv), s));
+    MP_CUDA_TRY(launch_col_absmax(n, nrhs, dR, ldr, sb->rnorm, &sb->st, s));
+    MP_CUDA_TRY(launch_trsv_lower<float>(n, nrhs, dW, ldw, at<float>(work, L.Linv), dR, ldr, perm, sb->rnorm,
+                                         at<float>(work, L.Y), n, at<int>(work, L.flagsL),
+                                         at<int>(work, L.tickets), 1, &sb->st, s));
+    MP_CUDA_TRY(launch_trsv_upper<float>(n, nrhs, dW, ldw, at<float>(work, L.Uinv), at<float>(work, L.Y), n,
+                                         at<float>(work, L.Z), n, at<int>(work, L.flagsU),
+                                         at<int>(work, L.tickets) + 1, 1, &sb->st, s));
+    MP_CUDA_TRY(launch_update<float>(n, nrhs, at<float>(work, L.Z), n, sb->rnorm, dZ, ldz, sb->znorm, 1, s));
+    StatusBlock h;
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h.st.flags & MP_FLAG_TIMEOUT) {
+        mp_set_error("triangular solve: a bounded wait gave up");
+        return -1000 - (int)cudaErrorLaunchTimeout;
+    }
+    return 0;
+}
+
+extern "C" int mp_residual(int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
+                           const double *dB, int ldb, double *dR, int ldr, void *work, size_t work_bytes,
+                           void *stream) {
+    g_err[0] = 0;
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 0 && !dA) return mp_arg_fail(3, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(4, "lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dX) return mp_arg_fail(5, "X is NULL");
+    if (ldx < std::max(1, n)) return mp_arg_fail(6, "ldx < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dB) return mp_arg_fail(7, "B is NULL");
+    if (ldb < std::max(1, n)) return mp_arg_fail(8, "ldb < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dR) return mp_arg_fail(9, "R is NULL");
+    if (ldr < std::max(1, n)) return mp_arg_fail(10, "ldr < max(1, n)");
+    StepLayout L = step_layout(n, nrhs, 32, MP_PREC_FP32);
+    if (!work) return mp_arg_fail(11, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(12, "workspace too small");
+    if (n == 0 || nrhs == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = at<StatusBlock>(work, L.status);
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(launch_residual_partial(n, nrhs, dA, lda, dX, ldx, at<double>(work, L.part), L.ksplit, s));
+    MP_CUDA_TRY(launch_residual_finalize(n, nrhs, at<double>(work, L.part), L.ksplit, dB, ldb, dX, ldx, dR,
+                                         ldr, sb->rnorm, sb->xnorm, &sb->st, s));
+    return 0;
+}
+
+extern "C" size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec) {
+    if (M < 0 || N < 0 || K < 0) return 0;
+    size_t off = 0;
+    carve(off, sizeof(StatusBlock));
+    carve(off, tc_workspace_bytes(std::max(M, N), K, prec));
+    return align_up(off, 256);
+}
+
+extern "C" int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl, const float *dU,
+                                   int ldu, float *dC, int ldc, void *work, size_t work_bytes, void *stream) {
+    g_err[0] = 0;
+    if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP16)
+        return mp_arg_fail(1, "prec must be FP32, BF16 or FP16");
+    if (M < 0) return mp_arg_fail(2, "M < 0");
+    if (N < 0) return mp_arg_fail(3, "N < 0");
+    if (K < 0) return mp_arg_fail(4, "K < 0");
+    if (M > 0 && K > 0 && !dL) return mp_arg_fail(5, "L is NULL");
+    if (ldl < std::max(1, K) || ldl % 4) return mp_arg_fail(6, "ldl must be >= K and a multiple of 4");
+    if (K > 0 && N > 0 && !dU) return mp_arg_fail(7, "U is NULL");
+    if (ldu < std::max(1, N) || ldu % 4) return mp_arg_fail(8, "ldu must be >= N and a multiple of 4");
+    if (M > 0 && N > 0 && !dC) return mp_arg_fail(9, "C is NULL");
+    if (ldc < std::max(1, N) || ldc % 4) return mp_arg_fail(10, "ldc must be >= N and a multiple of 4");
+    const size_t need = mp_lowp_gemm_workspace_bytes(M, N, K, prec);
+    if (!work) return mp_arg_fail(11, "workspace is NULL");
+    if (work_bytes < need) return mp_arg_fail(12, "workspace too small");
+    if (M == 0 || N == 0 || K == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t off = 0;
+    StatusBlock *sb = at<StatusBlock>(work, carve(off, sizeof(StatusBlock)));
+    void *tcws = at<void>(work, carve(off, tc_workspace_bytes(std::max(M, N), K, prec)));
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    if (prec == MP_PREC_FP32) {
+        MP_CUDA_TRY(launch_gemm_sub<float>(M, N, K, dL, ldl, dU, ldu, dC, ldc, s));
+    } else {
+        MP_CUDA_TRY(tc_trailing_update(prec, M, N, K, dL, ldl, dU, ldu, dC, ldc, tcws, &sb->st, s));
+    }
+    StatusBlock h;
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h.st.flags & MP_FLAG_TIMEOUT) {
+        mp_set_error("tensor-core update: a bounded wait gave up");
+        return -1000 - (int)cudaErrorLaunchTimeout;
+    }
+    return 0;
+}

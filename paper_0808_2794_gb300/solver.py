@@ -1,0 +1,338 @@
+"""Thin Python binding of the C ABI in ``include/mpsolve.h``.
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+``_build/libmpsolve.so`` (built by ``paper_0808_2794_gb300.build``).  There is
+no CPU fallback: if the library or a GPU is missing, these functions raise.
+
+Matrices are column-major (LAPACK layout).  A torch tensor ``A`` of shape
+(n, n) is column-major when ``A.stride() == (1, lda)``; ``colmajor(t)`` returns
+such a copy.  Workspace comes from PyTorch's caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PREC = {"fp32": 0, "tf32x3": 1, "bf16": 2, "fp16": 3, "e4m3": 4}
+REFINE = {"classical": 0, "gmres": 1, "auto": 2}
+
+FLAG_FALLBACK = 1
+FLAG_STALLED = 2
+FLAG_LOWP_BREAKDOWN = 4
+FLAG_NONFINITE_INPUT = 8
+FLAG_TIMEOUT = 16
+FLAG_GMRES_USED = 32
+FLAG_NOT_CONVERGED = 64
+
+
+class mp_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("refine", ctypes.c_int), ("itermax", ctypes.c_int),
+                ("tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("stall_ratio", ctypes.c_double),
+                ("allow_fallback", ctypes.c_int), ("nb_outer", ctypes.c_int),
+                ("nb_inner", ctypes.c_int)]
+
+
+class mp_stats(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int), ("flags", ctypes.c_uint), ("info", ctypes.c_int),
+                ("n_precond", ctypes.c_int), ("bwd_err", ctypes.c_double), ("nhist", ctypes.c_int),
+                ("hist", ctypes.c_double * 32), ("ms_convert", ctypes.c_float),
+                ("ms_factor", ctypes.c_float), ("ms_refine", ctypes.c_float),
+                ("ms_fallback", ctypes.c_float)]
+
+    def as_dict(self):
+        return dict(iter=self.iter, flags=self.flags, info=self.info, n_precond=self.n_precond,
+                    bwd_err=self.bwd_err, hist=list(self.hist[: self.nhist]),
+                    ms_convert=self.ms_convert, ms_factor=self.ms_factor,
+                    ms_refine=self.ms_refine, ms_fallback=self.ms_fallback)
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_Z = ctypes.c_size_t
+_SIGS = {
+    "mp_default_opts": (None, [ctypes.POINTER(mp_opts)]),
+    "mp_last_error": (ctypes.c_char_p, []),
+    "mp_gesv_workspace_bytes": (_Z, [_I, _I, ctypes.POINTER(mp_opts)]),
+    "mp_gesv": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _P, _Z, ctypes.POINTER(mp_opts),
+                     ctypes.POINTER(mp_stats), _P]),
+    "mp_gesv_host_workspace_bytes": (_Z, [_I, _I, ctypes.POINTER(mp_opts)]),
+    "mp_gesv_host": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _P, _Z, ctypes.POINTER(mp_opts),
+                          ctypes.POINTER(mp_stats), _P]),
+    "mp_factor_ld": (_I, [_I]),
+    "mp_getrf_workspace_bytes": (_Z, [_I, ctypes.POINTER(mp_opts)]),
+    "mp_convert": (_I, [_I, _P, _I, _P, _I, _P, _P, _P, _Z, _P]),
+    "mp_getrf_lowp": (_I, [_I, _P, _I, _P, ctypes.POINTER(mp_opts), _P, _Z,
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32), _P]),
+    "mp_getrs_workspace_bytes": (_Z, [_I, _I]),
+    "mp_getrs_lowp": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _I, _P, _Z, _P]),
+    "mp_residual_workspace_bytes": (_Z, [_I, _I]),
+    "mp_lowp_gemm_workspace_bytes": (_Z, [_I, _I, _I, _I]),
+    "mp_lowp_gemm_update": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _Z, _P]),
+    "mp_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _Z, _P]),
+    "mp_profile_enable": (None, [ctypes.c_uint]),
+    "mp_profile_collect": (_I, [_P, _P, _P]),
+    "mp_launch_count": (ctypes.c_longlong, []),
+}
+
+KERNEL_CLASSES = ["panel", "rowmoves", "trsm", "update", "panelgemm", "trsv", "residual"]
+
+
+def profile_enable(classes=()):
+    """Time the named kernel classes with CUDA events (empty: off, clears records)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KERNEL_CLASSES.index(c)
+    load().mp_profile_enable(mask)
+
+
+def profile_collect():
+    """{class: (ms, launches, work)} for the records since profile_enable."""
+    import numpy as np
+    ms = np.zeros(len(KERNEL_CLASSES))
+    ln = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+    wk = np.zeros(len(KERNEL_CLASSES))
+    _check(load().mp_profile_collect(ms.ctypes.data, ln.ctypes.data, wk.ctypes.data),
+           "mp_profile_collect")
+    return {c: (float(ms[i]), int(ln[i]), float(wk[i])) for i, c in enumerate(KERNEL_CLASSES)}
+
+
+def launch_count() -> int:
+    return int(load().mp_launch_count())
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects."""
+    return sorted(_SIGS)
+
+
+def load(build_if_missing: bool = True):
+    """Load libmpsolve.so (building it with nvcc if needed); raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library not built: {path}")
+                path = _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().mp_last_error().decode()
+
+
+def default_opts(**kw) -> mp_opts:
+    o = mp_opts()
+    load().mp_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        if k == "refine" and isinstance(v, str):
+            v = REFINE[v]
+        setattr(o, k, v)
+    return o
+
+
+class MpError(RuntimeError):
+    pass
+
+
+def _check(ret, what):
+    if ret < 0:
+        raise MpError(f"{what} returned {ret}: {last_error()}")
+    return ret
+
+
+# ---------------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise MpError("a CUDA device is required (there is no CPU path)")
+    return torch
+
+
+def colmajor(t):
+    """Column-major (Fortran-order) copy of a 2-D tensor (view if already)."""
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t):
+    """Leading dimension of a column-major 2-D tensor (any value >= rows for one column)."""
+    return t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0], t.stride(1))
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace(nbytes: int, device=None):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
+         nb_outer=0, work=None, stream=None):
+    """Solve A X = B (Algorithm 1).  A: (n, n) float64 CUDA tensor, B: (n,) or
+    (n, nrhs).  Returns (X, ipiv, stats) with X column-major float64 and ipiv
+    int32 (LAPACK 1-based)."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = B.dim() == 1
+    B = colmajor(B)
+    n, nrhs = B.shape
+    opts = default_opts(prec=prec, refine=refine, itermax=itermax, tol=tol,
+                        allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer)
+    X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    need = lib.mp_gesv_workspace_bytes(n, nrhs, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    st = mp_stats()
+    ret = lib.mp_gesv(n, nrhs, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(),
+                      _ld(X), ipiv.data_ptr(), work.data_ptr(), work.numel(),
+                      ctypes.byref(opts), ctypes.byref(st), _stream_ptr(stream))
+    _check(ret, "mp_gesv")
+    d = st.as_dict()
+    d["info_fp64"] = ret
+    return (X[:, 0] if squeeze else X), ipiv[:n], d
+
+
+def gesv_host(A, B, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True, nb_outer=0,
+              work=None, stream=None):
+    """Same as gesv with host (numpy, column-major float64) A and B; the host to
+    device copies happen inside the C call."""
+    import numpy as np
+    lib = load()
+    A = np.asfortranarray(A, dtype=np.float64)
+    squeeze = np.asarray(B).ndim == 1
+    B = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(A.shape[0], -1))
+    n, nrhs = B.shape
+    X = np.zeros((n, nrhs), dtype=np.float64, order="F")
+    ipiv = np.zeros(max(n, 1), dtype=np.int32)
+    opts = default_opts(prec=prec, itermax=itermax, tol=tol,
+                        allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer)
+    need = lib.mp_gesv_host_workspace_bytes(n, nrhs, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need)
+    st = mp_stats()
+    ret = lib.mp_gesv_host(n, nrhs, A.ctypes.data, n, B.ctypes.data, n, X.ctypes.data, n,
+                           ipiv.ctypes.data, work.data_ptr(), work.numel(), ctypes.byref(opts),
+                           ctypes.byref(st), _stream_ptr(stream))
+    _check(ret, "mp_gesv_host")
+    return (X[:, 0] if squeeze else X), ipiv[:n], st.as_dict()
+
+
+def factor_ld(n: int) -> int:
+    return load().mp_factor_ld(n)
+
+
+def convert(A, work=None, stream=None):
+    """W = fl32(A) (row-major, ld = factor_ld(n)) and ||A||_inf.  Returns (W, anorm, flags)."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    n = A.shape[0]
+    ldw = lib.mp_factor_ld(n)
+    W = torch.zeros((n, ldw), dtype=torch.float32, device=A.device)
+    anorm = torch.zeros(1, dtype=torch.float64, device=A.device)
+    flags = torch.zeros(1, dtype=torch.int32, device=A.device)
+    need = lib.mp_getrs_workspace_bytes(n, 1)
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    _check(lib.mp_convert(n, A.data_ptr(), _ld(A), W.data_ptr(), ldw, anorm.data_ptr(),
+                          flags.data_ptr(), work.data_ptr(), work.numel(), _stream_ptr(stream)),
+           "mp_convert")
+    return W, anorm, flags
+
+
+def getrf_lowp(W, prec="fp32", nb_outer=0, work=None, stream=None):
+    """In-place LU with partial pivoting of the row-major FP32 W (n x ldw).
+    Returns (ipiv, info, flags)."""
+    torch = _torch()
+    lib = load()
+    n, ldw = W.shape
+    opts = default_opts(prec=prec, nb_outer=nb_outer)
+    ipiv = torch.zeros(max(n, 1), dtype=torch.int32, device=W.device)
+    need = lib.mp_getrf_workspace_bytes(n, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need, W.device)
+    info = ctypes.c_int(0)
+    flags = ctypes.c_uint32(0)
+    _check(lib.mp_getrf_lowp(n, W.data_ptr(), ldw, ipiv.data_ptr(), ctypes.byref(opts),
+                             work.data_ptr(), work.numel(), ctypes.byref(info), ctypes.byref(flags),
+                             _stream_ptr(stream)), "mp_getrf_lowp")
+    return ipiv[:n], info.value, flags.value
+
+
+def getrs_lowp(W, ipiv, R, work=None, stream=None):
+    """z = U^{-1} L^{-1} P r with the FP32 factors (scaled by a power of two); FP64 in/out."""
+    torch = _torch()
+    lib = load()
+    n, ldw = W.shape
+    squeeze = R.dim() == 1
+    R = colmajor(R)
+    nrhs = R.shape[1]
+    Z = torch.empty((nrhs, n), dtype=torch.float64, device=W.device).t()
+    need = lib.mp_getrs_workspace_bytes(n, nrhs)
+    if work is None or work.numel() < need:
+        work = workspace(need, W.device)
+    _check(lib.mp_getrs_lowp(n, nrhs, W.data_ptr(), ldw, ipiv.data_ptr(), R.data_ptr(), _ld(R),
+                             Z.data_ptr(), _ld(Z), work.data_ptr(), work.numel(),
+                             _stream_ptr(stream)), "mp_getrs_lowp")
+    return Z[:, 0] if squeeze else Z
+
+
+def residual(A, X, B, work=None, stream=None):
+    """R = B - A X in FP64 (Algorithm 1 step 4)."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = X.dim() == 1
+    X = colmajor(X)
+    B = colmajor(B)
+    n, nrhs = X.shape
+    R = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    need = lib.mp_residual_workspace_bytes(n, nrhs)
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    _check(lib.mp_residual(n, nrhs, A.data_ptr(), _ld(A), X.data_ptr(), _ld(X),
+                           B.data_ptr(), _ld(B), R.data_ptr(), _ld(R), work.data_ptr(),
+                           work.numel(), _stream_ptr(stream)), "mp_residual")
+    return R[:, 0] if squeeze else R
+
+
+def lowp_gemm_update(C, L, U, prec="bf16", work=None, stream=None):
+    """C -= fl_p(L) fl_p(U) in place; C, L, U row-major (contiguous) FP32 CUDA tensors."""
+    lib = load()
+    M, K = L.shape
+    K2, N = U.shape
+    assert K == K2 and tuple(C.shape) == (M, N)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    need = lib.mp_lowp_gemm_workspace_bytes(M, N, K, p)
+    if work is None or work.numel() < need:
+        work = workspace(need, C.device)
+    _check(lib.mp_lowp_gemm_update(p, M, N, K, L.data_ptr(), L.stride(0), U.data_ptr(), U.stride(0),
+                                   C.data_ptr(), C.stride(0), work.data_ptr(), work.numel(),
+                                   _stream_ptr(stream)), "mp_lowp_gemm_update")
+    return C

@@ -83,6 +83,23 @@ def test_getrs_matches_exact_solve(orc, n):
         assert abs(x[i] - float(x_ex[i])) <= 10 * kappa * U64 * max(abs(float(v)) for v in x_ex)
 
 
+@pytest.mark.parametrize("n", [3, 5, 8])
+@pytest.mark.parametrize("seed", range(4))
+def test_refined_solution_matches_exact_solve(orc, n, seed):
+    """Algorithm 1 with an FP32 factor, run to the FP64 floor, gives the exact
+    solution to within 10 kappa_inf u64 (forward error) and bwd <= 1e-14."""
+    A = inputs.small_integer_matrix(n, seed=50 + 10 * n + seed)
+    A[np.diag_indices(n)] += 10.0
+    Af = exact.to_frac_matrix(A.tolist())
+    b = np.arange(1.0, n + 1) * (-1) ** np.arange(n)
+    x_ex = np.array([float(v) for v in exact.solve(Af, [Fraction(v) for v in b])])
+    inv = exact.inverse(Af)
+    kappa = float(exact.norm_inf(Af) * exact.norm_inf(inv))
+    r = orc.gesv_ir(A, b, factor_prec=32)
+    assert r["flags"] == 0 and r["bwd"] <= 1e-14
+    assert np.max(np.abs(r["X"] - x_ex)) <= 10 * kappa * U64 * np.max(np.abs(x_ex))
+
+
 def test_singular_matrix_reports_info(orc):
     A = inputs.small_integer_matrix(6, seed=3)
     A[4, :] = A[1, :]  # duplicate rows
