@@ -50,11 +50,13 @@ def host(t):
 
 def unambiguous_matrix(n, seed):
     """A = P0^T L0 U0 with |l_ij| <= 1/(2 sqrt(n)): exact partial pivoting
-    picks the rows of P0 with a margin of 2 sqrt(n) at every step, and L0 stays
-    well conditioned, so rounding cannot change a pivot decision."""
+    picks the rows of P0 with a margin of 2 sqrt(n) at every step.  L0 and U0
+    (off-diagonal entries O(1/sqrt(n)), |u_ii| in [1, 2]) are well conditioned,
+    so no rounding order can change a pivot decision."""
     rng = np.random.default_rng(seed)
     L0 = np.tril(rng.uniform(-0.5, 0.5, (n, n)) / np.sqrt(n), -1) + np.eye(n)
-    U0 = np.triu(rng.uniform(-1, 1, (n, n)), 1) + np.diag(rng.uniform(1, 2, n) * rng.choice([-1, 1], n))
+    U0 = (np.triu(rng.uniform(-1, 1, (n, n)), 1) / np.sqrt(n)
+          + np.diag(rng.uniform(1, 2, n) * rng.choice([-1, 1], n)))
     perm = rng.permutation(n)
     A = np.empty((n, n))
     A[perm, :] = L0 @ U0  # row perm[i] of A is row i of L0 U0
