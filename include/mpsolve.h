@@ -130,6 +130,31 @@ MP_API int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const double
                  double *hX, int ldx, int32_t *hipiv, void *work, size_t work_bytes,
                  const mp_opts *opts, mp_stats *stats, void *stream);
 
+/* Allocation-free variant of mp_gesv (the paper has no counterpart; this is
+ * a deployment convenience).  Some callers may not call cudaMalloc: code that
+ * runs while a CUDA graph is being captured, services that fix their device
+ * memory at start-up and forbid allocation afterwards (an allocation can
+ * synchronize the device and can fail under memory pressure), and plug-ins
+ * whose host framework owns every device allocation.  This entry point takes
+ * its scratch from a static device array of MP_NOALLOC_SCRATCH_BYTES that is
+ * part of the library image: every GPU that loads the library holds that
+ * memory until the process exits.  The caller still passes A, B, X and ipiv
+ * (device pointers, as for mp_gesv); the call allocates nothing.
+ *   - Sizes whose mp_gesv_workspace_bytes(n, nrhs, opts) exceed the array
+ *     return -1 with an explanatory mp_last_error().
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the previous
+ *     call's contents; the solver re-initializes everything it needs.  Calls
+ *     that overlap on the GPU (different streams or host threads) race on the
+ *     array: serialize them.
+ *   - Phase times in mp_stats are not measured (left 0). */
+#define MP_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+MP_API size_t mp_noalloc_scratch_bytes(void);
+MP_API int mp_gesv_noalloc(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
+                           double *dX, int ldx, int32_t *dipiv, const mp_opts *opts,
+                           mp_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------------
  * Steps of the hot path, exposed for testing and for callers that keep
  * the factors (Section 3.1.1: SGETRF, SGETRS, DGEMM residual, DAXPY).

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "driver.cuh"
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
 
@@ -479,6 +480,13 @@ extern "C" size_t mp_gesv_workspace_bytes(int n, int nrhs, const mp_opts *opts) 
 extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
                        double *dX, int ldx, int32_t *dipiv, void *work, size_t work_bytes,
                        const mp_opts *opts, mp_stats *stats, void *stream) {
+    return mp_gesv_impl(n, nrhs, dA, lda, dB, ldb, dX, ldx, dipiv, work, work_bytes, opts, stats, stream,
+                        stats != nullptr);
+}
+
+int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+                 int ldx, int32_t *dipiv, void *work, size_t work_bytes, const mp_opts *opts,
+                 mp_stats *stats, void *stream, bool timing) {
     g_err[0] = 0;
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
@@ -505,7 +513,6 @@ extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Solve S{n, nrhs, dA, lda, dB, ldb, dX, ldx, work, L, s, at<StatusBlock>(work, L.status), 0};
     cudaEvent_t ev[5] = {};
-    const bool timing = stats != nullptr;
     if (timing)
         for (auto &e : ev) MP_CUDA_TRY(cudaEventCreate(&e));
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
@@ -571,7 +578,7 @@ extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double 
     if (stats) {
         stats->iter = iters;
         stats->flags = flags;
-        if (timing) {
+        if (timing && stats) {
             cudaEventElapsedTime(&stats->ms_convert, ev[0], ev[1]);
             cudaEventElapsedTime(&stats->ms_factor, ev[1], ev[2]);
             cudaEventElapsedTime(&stats->ms_refine, ev[2], ev[3]);

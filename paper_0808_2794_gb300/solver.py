@@ -76,6 +76,9 @@ _SIGS = {
     "mp_lowp_gemm_workspace_bytes": (_Z, [_I, _I, _I, _I]),
     "mp_lowp_gemm_update": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _Z, _P]),
     "mp_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _Z, _P]),
+    "mp_noalloc_scratch_bytes": (_Z, []),
+    "mp_gesv_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(mp_opts),
+                             ctypes.POINTER(mp_stats), _P]),
     "mp_profile_enable": (None, [ctypes.c_uint]),
     "mp_profile_collect": (_I, [_P, _P, _P]),
     "mp_launch_count": (ctypes.c_longlong, []),
