@@ -80,11 +80,18 @@ compose_swaps_kernel(const int32_t *__restrict__ ipiv, int k1, int k2, int n, in
 template <typename T, int CW>
 __global__ void __launch_bounds__(256)
 apply_moves_kernel(T *__restrict__ W, long ld, const int2 *__restrict__ pairs,
-                   const int *__restrict__ npairs, int c0, int c1, int c2, int c3) {
+                   const int *__restrict__ npairs, int c0, int c1, int c2, int c3, int *perm) {
     extern __shared__ unsigned char dyn_raw[];
     T *tile = reinterpret_cast<T *>(dyn_raw);
     const int np = *npairs;
     if (np == 0) return;
+    if (perm && blockIdx.x == gridDim.x - 1) {  // the last CTA also permutes perm
+        int *pv = reinterpret_cast<int *>(tile);
+        for (int t = threadIdx.x; t < np; t += blockDim.x) pv[t] = perm[pairs[t].y];
+        __syncthreads();
+        for (int t = threadIdx.x; t < np; t += blockDim.x) perm[pairs[t].x] = pv[t];
+        __syncthreads();
+    }
     const int nch1 = (c1 - c0 + CW - 1) / CW;
     int cs, ce;
     if ((int)blockIdx.x < nch1) {
@@ -95,6 +102,7 @@ apply_moves_kernel(T *__restrict__ W, long ld, const int2 *__restrict__ pairs,
         ce = min(cs + CW, c3);
     }
     const int w = ce - cs;
+    if (w <= 0) return;
     for (int idx = threadIdx.x; idx < np * CW; idx += blockDim.x) {
         const int pr = idx / CW, cc = idx - pr * CW;
         if (cc < w) tile[idx] = W[(long)pairs[pr].y * ld + cs + cc];
@@ -133,23 +141,28 @@ cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int
 
 template <typename T>
 cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
-                               int c0, int c1, int c2, int c3, cudaStream_t s) {
+                               int c0, int c1, int c2, int c3, int *perm, cudaStream_t s) {
     constexpr int CW = 128 / sizeof(T);  // 128-byte row segments
-    const int nch = (c1 > c0 ? (c1 - c0 + CW - 1) / CW : 0) + (c3 > c2 ? (c3 - c2 + CW - 1) / CW : 0);
-    if (nch == 0 || max_pairs == 0) return cudaSuccess;
     if (c1 < c0) c1 = c0;
+    if (c3 < c2) c3 = c2;
+    int nch = (c1 - c0 + CW - 1) / CW + (c3 - c2 + CW - 1) / CW;
+    if (max_pairs == 0) return cudaSuccess;
+    if (nch == 0) {
+        if (!perm) return cudaSuccess;
+        nch = 1;  // perm only: one CTA whose column ranges are empty
+    }
     size_t smem = (size_t)max_pairs * CW * sizeof(T);
     auto kern = apply_moves_kernel<T, CW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     mp_note_launch();
-    kern<<<nch, 256, smem, s>>>(W, ld, pairs, npairs, c0, c1, c2, c3);
+    kern<<<nch, 256, smem, s>>>(W, ld, pairs, npairs, c0, c1, c2, c3, perm);
     return cudaGetLastError();
 }
 template cudaError_t launch_apply_moves<float>(float *, long, const int2 *, const int *, int, int,
-                                               int, int, int, cudaStream_t);
+                                               int, int, int, int *, cudaStream_t);
 template cudaError_t launch_apply_moves<double>(double *, long, const int2 *, const int *, int,
-                                                int, int, int, int, cudaStream_t);
+                                                int, int, int, int, int *, cudaStream_t);
 
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s) {

@@ -9,10 +9,12 @@
 template <typename T> int panel_base_width(int m);
 // LU with partial pivoting of the m x ncols panel starting at P (row-major, ld),
 // ncols <= panel_base_width<T>(m).  ipiv[j] (j < ncols) receives the global
-// 1-based pivot row row0 + p + 1.
+// 1-based pivot row row0 + p + 1; moves[0 .. *nmoves) receives the composed
+// row permutation of the panel as (destination row, source row) pairs
+// (global row indices, at most 2 * ncols).
 template <typename T>
-cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv,
-                         MpDevStatus *st, cudaStream_t s);
+cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
+                         int *nmoves, MpDevStatus *st, cudaStream_t s);
 
 // ---- row exchanges (blas3.cu) ---------------------------------------------
 // Composes the swaps ipiv[k1..k2) (1-based rows) into a list of (dst, src)
@@ -20,10 +22,11 @@ cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipi
 // n ints (identity on entry, restored on exit) for tall matrices.
 cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int2 *pairs,
                                  int *npairs, int *map_scratch, cudaStream_t s);
-// Applies the moves to columns [c0,c1) and [c2,c3) of W.
+// Applies the moves to columns [c0,c1) and [c2,c3) of W, and (if perm is not
+// null) to the row permutation vector perm.
 template <typename T>
 cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
-                               int c0, int c1, int c2, int c3, cudaStream_t s);
+                               int c0, int c1, int c2, int c3, int *perm, cudaStream_t s);
 // Applies the moves to an int vector (the running row permutation).
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s);
@@ -47,20 +50,23 @@ cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, 
 cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s);
 
 // ---- triangular solves with the factors (trsv.cu) ---------------------------
-constexpr int TRSV_BS = 64;
+// Block size of the blocked solves: 128 rows (FP32), 64 rows (FP64).
+template <typename T> int trsv_block_size();
+// Bytes of the per-chunk partial-sum slots for order n, block size bs.
+size_t trsv_slot_bytes(int n, int bs, size_t elem);
 template <typename T>
 cudaError_t launch_diag_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, cudaStream_t s);
-// Lower solve: Y[:,c] = Linv-blocked solve of (P r_c) / s_c, where r is FP64
-// col-major (ldr), perm the row permutation, s_c = 2^ceil(log2 rnorm[c]).
+// Lower solve: Y[:,c] = L^{-1} (P r_c) / s_c, r FP64 col-major (ldr), perm the
+// row permutation, s_c = 2^ceil(log2 rnorm[c]).  flags/counts: one int per
+// block (zero before the first epoch), ticket: one int; epoch = 1, 2, ...
 template <typename T>
-cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv,
-                              const double *R, long ldr, const int *perm, const double *rnorm,
-                              T *Y, long ldy, int *flags, int *ticket, int epoch,
+cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv, const double *R, long ldr,
+                              const int *perm, const double *rnorm, T *Y, long ldy, T *slots, int *flags,
+                              int *counts, int *ticket, int epoch, MpDevStatus *st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trsv_upper(int n, int nrhs, const T *W, long ldw, const T *Uinv, const T *Y, long ldy, T *Z,
+                              long ldz, T *slots, int *flags, int *counts, int *ticket, int epoch,
                               MpDevStatus *st, cudaStream_t s);
-template <typename T>
-cudaError_t launch_trsv_upper(int n, int nrhs, const T *W, long ldw, const T *Uinv,
-                              const T *Y, long ldy, T *Z, long ldz, int *flags, int *ticket,
-                              int epoch, MpDevStatus *st, cudaStream_t s);
 
 // ---- FP64 residual and update (refine.cu) -----------------------------------
 int residual_ksplit(int n, int nrhs);

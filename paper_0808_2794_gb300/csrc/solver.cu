@@ -145,7 +145,7 @@ int outer_nb(int n, const mp_opts &o) {
 // ---------------------------------------------------------------------------
 struct Layout {
     size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, flagsL, flagsU,
-        tickets, R, Y, Z, part, tc, total;
+        countsL, countsU, slots, tickets, R, Y, Z, part, tc, total;
     size_t W_bytes;
     int ldw, nblk, ksplit, nb;
 };
@@ -161,7 +161,7 @@ size_t carve(size_t &off, size_t bytes) {
 Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
     Layout L{};
     L.ldw = mp_factor_ld(n);
-    L.nblk = (n + TRSV_BS - 1) / TRSV_BS;
+    L.nblk = (n + 63) / 64;  // blocks of the FP64 solve (the FP32 solve uses half as many)
     L.ksplit = residual_ksplit(n, nrhs);
     L.nb = outer_nb(n, o);
     const size_t el = fp64_space ? sizeof(double) : sizeof(float);
@@ -176,10 +176,16 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, L.nb));
     L.npairs = carve(off, sizeof(int) * 4);
     L.map = carve(off, sizeof(int) * (size_t)n);
-    L.Linv = carve(off, el * (size_t)L.nblk * TRSV_BS * TRSV_BS);
-    L.Uinv = carve(off, el * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    const size_t inv_bytes = std::max((size_t)((n + 127) / 128) * 128 * 128 * sizeof(float),
+                                      fp64_space ? (size_t)L.nblk * 64 * 64 * sizeof(double) : 0);
+    L.Linv = carve(off, inv_bytes);
+    L.Uinv = carve(off, inv_bytes);
     L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
     L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.countsL = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.countsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.slots = carve(off, std::max(trsv_slot_bytes(n, 128, sizeof(float)),
+                                  fp64_space ? trsv_slot_bytes(n, 64, sizeof(double)) : 0));
     L.tickets = carve(off, sizeof(int) * 4);
     L.R = carve(off, sizeof(double) * (size_t)n * rhs);
     L.Y = carve(off, el * (size_t)n * rhs);
@@ -242,19 +248,12 @@ cudaError_t trsm_rec(int m, int N, const T *L, long ldl, T *B, long ldb, cudaStr
     return trsm_rec<T>(m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb, s);
 }
 
-// Applies the swaps ipiv[k1..k2) to columns [c0,c1) and [c2,c3).
-template <typename T>
-cudaError_t row_moves(FactorCtx<T> &c, int k1, int k2, int c0, int c1, int c2, int c3, bool perm) {
-    MpProfScope ps(MP_KC_ROWMOVES, 4.0 * (k2 - k1) * ((c1 - c0) + (c3 - c2)) * sizeof(T), c.s);
-    CU(launch_compose_swaps(c.ipiv, k1, k2, c.n, c.pairs, c.npairs, c.map, c.s));
-    CU(launch_apply_moves<T>(c.W, c.ld, c.pairs, c.npairs, 2 * (k2 - k1), c0, c1, c2, c3, c.s));
-    if (perm) CU(launch_apply_moves_vec(c.perm, c.pairs, c.npairs, 2 * (k2 - k1), c.s));
-    return cudaSuccess;
-}
-
-// Recursive LU of the columns [k0, k0+ncols) of rows [k0, n): left half,
-// update of the right half (row moves, triangular solve, FP32 GEMM), right
-// half, then the right half's row moves applied to the left half.
+// Recursive LU of the columns [k0, k0+ncols) of rows [k0, n) (a recursive
+// panel): left half, U12 = L11^{-1} A12 and A22 -= L21 U12 (FP32) on the
+// right half, right half.  A leaf (ncols <= base width) is one cluster panel
+// kernel followed by the exchange of its rows over all other columns of W
+// (and the running row permutation), so every level sees rows in the
+// current pivoted order.
 template <typename T>
 cudaError_t getrf_rec(FactorCtx<T> &c, int k0, int ncols) {
     const int m = c.n - k0;
@@ -262,25 +261,28 @@ cudaError_t getrf_rec(FactorCtx<T> &c, int k0, int ncols) {
     T *W = c.W;
     const long ld = c.ld;
     if (ncols <= nb) {
-        MpProfScope ps(MP_KC_PANEL, (double)m * ncols * ncols - (double)ncols * ncols * ncols / 3.0, c.s);
-        return launch_panel<T>(W + (long)k0 * ld + k0, ld, m, ncols, k0, c.ipiv + k0, c.st, c.s);
+        {
+            MpProfScope ps(MP_KC_PANEL, (double)m * ncols * ncols - (double)ncols * ncols * ncols / 3.0, c.s);
+            CU(launch_panel<T>(W + (long)k0 * ld + k0, ld, m, ncols, k0, c.ipiv + k0, c.pairs, c.npairs, c.st, c.s));
+        }
+        MpProfScope ps(MP_KC_ROWMOVES, 4.0 * ncols * (double)(c.n - ncols) * sizeof(T), c.s);
+        return launch_apply_moves<T>(W, ld, c.pairs, c.npairs, 2 * ncols, 0, k0, k0 + ncols, c.n, c.perm, c.s);
     }
     int n1 = (ncols / 2) / nb * nb;
     if (n1 < nb) n1 = nb;
     CU(getrf_rec<T>(c, k0, n1));
-    CU(row_moves<T>(c, k0, k0 + n1, k0 + n1, k0 + ncols, 0, 0, false));
     {
         MpProfScope ps(MP_KC_PANELGEMM, (double)n1 * n1 * (ncols - n1) + 2.0 * (m - n1) * (ncols - n1) * n1, c.s);
         CU(trsm_rec<T>(n1, ncols - n1, W + (long)k0 * ld + k0, ld, W + (long)k0 * ld + k0 + n1, ld, c.s));
         CU(launch_gemm_sub<T>(m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
                               W + (long)k0 * ld + k0 + n1, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld, c.s));
     }
-    CU(getrf_rec<T>(c, k0 + n1, ncols - n1));
-    return row_moves<T>(c, k0 + n1, k0 + ncols, k0, k0 + n1, 0, 0, false);
+    return getrf_rec<T>(c, k0 + n1, ncols - n1);
 }
 
-// Blocked right-looking LU: panel of width nb (recursive), row moves on the
-// rest of the matrix, U12 = L11^{-1} A12, A22 -= L21 U12 at precision prec.
+// Blocked right-looking LU: panel of width nb (recursive, rows exchanged over
+// the whole matrix as each leaf finishes), U12 = L11^{-1} A12, A22 -= L21 U12
+// at precision prec.
 template <typename T>
 cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     const int n = c.n;
@@ -289,7 +291,6 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     for (int k = 0; k < n; k += nb) {
         const int nbk = std::min(nb, n - k);
         CU(getrf_rec<T>(c, k, nbk));
-        CU(row_moves<T>(c, k, k + nbk, 0, k, k + nbk, n, true));
         const int rest = n - k - nbk;
         if (rest > 0) {
             {
@@ -345,10 +346,12 @@ int lowp_solve(Solve &S, const double *R, long ldr, const double *rnorm) {
     MpProfScope ps(MP_KC_TRSV, (double)S.n * S.n * sizeof(T) + 4.0 * S.n * S.nrhs * sizeof(T), S.s);
     MP_CUDA_TRY(launch_trsv_lower<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Linv), R, ldr,
                                      at<int>(S.work, L.perm), rnorm, at<T>(S.work, L.Y), S.n,
-                                     at<int>(S.work, L.flagsL), at<int>(S.work, L.tickets), S.epoch,
+                                     at<T>(S.work, L.slots), at<int>(S.work, L.flagsL),
+                                     at<int>(S.work, L.countsL), at<int>(S.work, L.tickets), S.epoch,
                                      &S.sb->st, S.s));
     MP_CUDA_TRY(launch_trsv_upper<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Uinv), at<T>(S.work, L.Y),
-                                     S.n, at<T>(S.work, L.Z), S.n, at<int>(S.work, L.flagsU),
+                                     S.n, at<T>(S.work, L.Z), S.n, at<T>(S.work, L.slots),
+                                     at<int>(S.work, L.flagsU), at<int>(S.work, L.countsU),
                                      at<int>(S.work, L.tickets) + 1, S.epoch, &S.sb->st, S.s));
     return 0;
 }
@@ -370,6 +373,8 @@ int reset_sync(Solve &S) {
     const Layout &L = S.L;
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsL), 0, sizeof(int) * L.nblk, S.s));
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsU), 0, sizeof(int) * L.nblk, S.s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.countsL), 0, sizeof(int) * L.nblk, S.s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.countsU), 0, sizeof(int) * L.nblk, S.s));
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.tickets), 0, sizeof(int) * 4, S.s));
     S.epoch = 0;
     return 0;
@@ -643,13 +648,13 @@ extern "C" int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const do
 // ---------------------------------------------------------------------------
 namespace {
 struct StepLayout {
-    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, flagsL, flagsU, tickets, Y, Z, part,
-        tc, total;
+    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, flagsL, flagsU, countsL, countsU, slots,
+        tickets, Y, Z, part, tc, total;
     int nblk, ksplit;
 };
 StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     StepLayout L{};
-    L.nblk = (n + TRSV_BS - 1) / TRSV_BS;
+    L.nblk = (n + 127) / 128;
     L.ksplit = residual_ksplit(std::max(n, 1), std::max(nrhs, 1));
     const int rhs = std::max(nrhs, 1);
     size_t off = 0;
@@ -659,10 +664,13 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, nb));
     L.npairs = carve(off, sizeof(int) * 4);
     L.map = carve(off, sizeof(int) * (size_t)n);
-    L.Linv = carve(off, sizeof(float) * (size_t)L.nblk * TRSV_BS * TRSV_BS);
-    L.Uinv = carve(off, sizeof(float) * (size_t)L.nblk * TRSV_BS * TRSV_BS);
+    L.Linv = carve(off, sizeof(float) * (size_t)L.nblk * 128 * 128);
+    L.Uinv = carve(off, sizeof(float) * (size_t)L.nblk * 128 * 128);
     L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
     L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.countsL = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.countsU = carve(off, sizeof(int) * (size_t)L.nblk);
+    L.slots = carve(off, trsv_slot_bytes(n, 128, sizeof(float)));
     L.tickets = carve(off, sizeof(int) * 4);
     L.Y = carve(off, sizeof(float) * (size_t)n * rhs);
     L.Z = carve(off, sizeof(float) * (size_t)n * rhs);
@@ -767,6 +775,8 @@ extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const in
     MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsL), 0, sizeof(int) * L.nblk, s));
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsU), 0, sizeof(int) * L.nblk, s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.countsL), 0, sizeof(int) * L.nblk, s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.countsU), 0, sizeof(int) * L.nblk, s));
     MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.tickets), 0, sizeof(int) * 4, s));
     // row permutation from the pivots: compose all n swaps, apply to identity
     int *perm = at<int>(work, L.perm);
@@ -783,10 +793,12 @@ extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const in
     MP_CUDA_TRY(launch_diag_inverses<float>(n, dW, ldw, at<float>(work, L.Linv), at<float>(work, L.Uinv), s));
     MP_CUDA_TRY(launch_col_absmax(n, nrhs, dR, ldr, sb->rnorm, &sb->st, s));
     MP_CUDA_TRY(launch_trsv_lower<float>(n, nrhs, dW, ldw, at<float>(work, L.Linv), dR, ldr, perm, sb->rnorm,
-                                         at<float>(work, L.Y), n, at<int>(work, L.flagsL),
+                                         at<float>(work, L.Y), n, at<float>(work, L.slots),
+                                         at<int>(work, L.flagsL), at<int>(work, L.countsL),
                                          at<int>(work, L.tickets), 1, &sb->st, s));
     MP_CUDA_TRY(launch_trsv_upper<float>(n, nrhs, dW, ldw, at<float>(work, L.Uinv), at<float>(work, L.Y), n,
-                                         at<float>(work, L.Z), n, at<int>(work, L.flagsU),
+                                         at<float>(work, L.Z), n, at<float>(work, L.slots),
+                                         at<int>(work, L.flagsU), at<int>(work, L.countsU),
                                          at<int>(work, L.tickets) + 1, 1, &sb->st, s));
     MP_CUDA_TRY(launch_update<float>(n, nrhs, at<float>(work, L.Z), n, sb->rnorm, dZ, ldz, sb->znorm, 1, s));
     StatusBlock h;
