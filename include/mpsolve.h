@@ -49,7 +49,9 @@ extern "C" {
 /* Precision of the O(n^3) factorization (Algorithm 1 step 1 at eps_s). */
 typedef enum {
     MP_PREC_FP32 = 0,   /* all factorization arithmetic in FP32 (the paper's single) */
-    MP_PREC_TF32X3 = 1, /* trailing update on tensor cores, 3 TF32 products (~FP32 accuracy) */
+    MP_PREC_FP16X3 = 1, /* trailing-update operands split into two fp16 parts (hi + lo, power-of-two
+                           scaled), three tensor-core products hi*hi + hi*lo + lo*hi with FP32
+                           accumulation: about FP32 accuracy at fp16 tensor-core speed */
     MP_PREC_BF16 = 2,   /* trailing-update operands rounded to bfloat16, FP32 accumulation */
     MP_PREC_FP16 = 3,   /* trailing-update operands rounded to binary16, FP32 accumulation */
     MP_PREC_E4M3 = 4    /* reserved: FP8 E4M3 with per-block power-of-two scales */
@@ -184,7 +186,8 @@ MP_API int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp_opt
 
 /* Solve with the FP32 factors (Algorithm 1 steps 5-6):
  * dZ = s * U^{-1} L^{-1} P (dR / s) computed in FP32, s = 2^ceil(log2 ||r||inf)
- * per column (exact scaling), returned in FP64.  dR, dZ: n x nrhs FP64
+ * per column (exact scaling), returned in FP64.  dW must be 16-byte aligned
+ * with ldw a multiple of 4 (mp_factor_ld(n) is).  dR, dZ: n x nrhs FP64
  * column-major (nrhs <= 8).  work must hold mp_getrs_workspace_bytes(n, nrhs). */
 MP_API size_t mp_getrs_workspace_bytes(int n, int nrhs);
 MP_API int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const int32_t *dipiv,
@@ -196,7 +199,8 @@ MP_API int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const int32_
  * with all three arrays FP32 ROW-major on the device (ldl >= K, ldu >= N,
  * ldc >= N; ldl, ldu, ldc multiples of 4).  prec: MP_PREC_FP32 (plain FP32
  * FMA on CUDA cores), MP_PREC_BF16 / MP_PREC_FP16 (operands rounded to
- * nearest even, FP32 accumulation on tcgen05 tensor cores).  work must hold
+ * nearest even, FP32 accumulation on tcgen05 tensor cores), MP_PREC_FP16X3
+ * (split operands, three tensor-core products).  work must hold
  * mp_lowp_gemm_workspace_bytes(M, N, K, prec). */
 MP_API size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec);
 MP_API int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl,

@@ -182,33 +182,45 @@ cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs,
 // ============================================================================
 namespace {
 
+// Batch addressing: entry z has offset (z / inner) * s_outer + (z % inner) * s_inner.
+struct BatchStride {
+    long s_outer, s_inner;
+    __device__ __forceinline__ long off(int z, int inner) const {
+        return (long)(z / inner) * s_outer + (long)(z % inner) * s_inner;
+    }
+};
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(256)
-gemm_sub_kernel(int M, int N, int K, const T *__restrict__ A, long lda,
-                const T *__restrict__ B, long ldb, T *__restrict__ C, long ldc) {
+gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long lda,
+            const T *__restrict__ B0, long ldb, T *__restrict__ C0, long ldc, int inner,
+            BatchStride sa, BatchStride sb, BatchStride sc) {
     static_assert((BM / TM) * (BN / TN) == 256, "thread layout");
     constexpr int TX = BN / TN;          // threads along N
     constexpr int A_ELEMS = BM * BK / 256;
     constexpr int B_ELEMS = BK * BN / 256;
     __shared__ T As[2][BK][BM];
     __shared__ T Bs[2][BK][BN];
+    const int z = blockIdx.z;
+    const T *A = A0 + sa.off(z, inner);
+    const T *B = B0 + sb.off(z, inner);
+    T *C = C0 + sc.off(z, inner);
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
 
-    // A tile loader: element e of thread -> (row, k)
     T ra[A_ELEMS], rb[B_ELEMS];
     auto load_tiles = [&](int k0) {
 #pragma unroll
         for (int e = 0; e < A_ELEMS; ++e) {
-            const int lin = tid * A_ELEMS + e;      // contiguous along k within a row
+            const int lin = tid * A_ELEMS + e;  // contiguous along k within a row
             const int r = lin / BK, kk = lin % BK;
             const int gr = m0 + r, gk = k0 + kk;
             ra[e] = (gr < M && gk < K) ? A[(long)gr * lda + gk] : T(0);
         }
 #pragma unroll
         for (int e = 0; e < B_ELEMS; ++e) {
-            const int lin = tid * B_ELEMS + e;      // contiguous along n within a k-row
+            const int lin = tid * B_ELEMS + e;  // contiguous along n within a k-row
             const int kk = lin / BN, c = lin % BN;
             const int gk = k0 + kk, gc = n0 + c;
             rb[e] = (gk < K && gc < N) ? B[(long)gk * ldb + gc] : T(0);
@@ -234,8 +246,10 @@ gemm_sub_kernel(int M, int N, int K, const T *__restrict__ A, long lda,
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
     const int KT = (K + BK - 1) / BK;
-    load_tiles(0);
-    store_tiles(0);
+    if (KT > 0) {
+        load_tiles(0);
+        store_tiles(0);
+    }
     __syncthreads();
     for (int kt = 0; kt < KT; ++kt) {
         const int cur = kt & 1;
@@ -269,33 +283,68 @@ gemm_sub_kernel(int M, int N, int K, const T *__restrict__ A, long lda,
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int c = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + (j - TN / 2));
-            if (c < N) crow[c] -= acc[i][j];
+            if (c < N) crow[c] = (beta == T(0) ? T(0) : beta * crow[c]) + alpha * acc[i][j];
         }
     }
 }
 
-}  // namespace
+template <typename T>
+cudaError_t gemm_launch(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,
+                        T *C, long ldc, int batch, int inner, BatchStride sa, BatchStride sb, BatchStride sc,
+                        cudaStream_t s);
 
 template <>
-cudaError_t launch_gemm_sub<float>(int M, int N, int K, const float *A, long lda, const float *B,
-                                   long ldb, float *C, long ldc, cudaStream_t s) {
-    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+cudaError_t gemm_launch<float>(int M, int N, int K, float alpha, float beta, const float *A, long lda,
+                               const float *B, long ldb, float *C, long ldc, int batch, int inner,
+                               BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s) {
     constexpr int BM = 128, BN = 128, BK = 8;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     mp_note_launch();
-    gemm_sub_kernel<float, BM, BN, BK, 8, 8><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    gemm_kernel<float, BM, BN, BK, 8, 8><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C, ldc,
+                                                              inner, sa, sb, sc);
     return cudaGetLastError();
 }
 template <>
-cudaError_t launch_gemm_sub<double>(int M, int N, int K, const double *A, long lda, const double *B,
-                                    long ldb, double *C, long ldc, cudaStream_t s) {
-    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+cudaError_t gemm_launch<double>(int M, int N, int K, double alpha, double beta, const double *A, long lda,
+                                const double *B, long ldb, double *C, long ldc, int batch, int inner,
+                                BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s) {
     constexpr int BM = 64, BN = 64, BK = 16;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     mp_note_launch();
-    gemm_sub_kernel<double, BM, BN, BK, 4, 4><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    gemm_kernel<double, BM, BN, BK, 4, 4><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C, ldc,
+                                                               inner, sa, sb, sc);
     return cudaGetLastError();
 }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_gemm_sub(int M, int N, int K, const T *A, long lda, const T *B, long ldb, T *C, long ldc,
+                            cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    const BatchStride z{0, 0};
+    return gemm_launch<T>(M, N, K, T(-1), T(1), A, lda, B, ldb, C, ldc, 1, 1, z, z, z, s);
+}
+template cudaError_t launch_gemm_sub<float>(int, int, int, const float *, long, const float *, long, float *,
+                                            long, cudaStream_t);
+template cudaError_t launch_gemm_sub<double>(int, int, int, const double *, long, const double *, long,
+                                             double *, long, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_gemm_batched(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,
+                                T *C, long ldc, int batch, int inner, long a_outer, long a_inner, long b_outer,
+                                long b_inner, long c_outer, long c_inner, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+    return gemm_launch<T>(M, N, K, alpha, beta, A, lda, B, ldb, C, ldc, batch, inner,
+                          BatchStride{a_outer, a_inner}, BatchStride{b_outer, b_inner},
+                          BatchStride{c_outer, c_inner}, s);
+}
+template cudaError_t launch_gemm_batched<float>(int, int, int, float, float, const float *, long, const float *,
+                                                long, float *, long, int, int, long, long, long, long, long, long,
+                                                cudaStream_t);
+template cudaError_t launch_gemm_batched<double>(int, int, int, double, double, const double *, long,
+                                                 const double *, long, double *, long, int, int, long, long, long,
+                                                 long, long, long, cudaStream_t);
 
 // ============================================================================
 // B[m x N] <- L^{-1} B, L unit lower triangular (m <= 64).  One thread per
@@ -314,19 +363,40 @@ trsm_llnu_small_kernel(int m, int N, const T *__restrict__ L, long ldl, T *__res
     __syncthreads();
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= N) return;
-    T b[64];
+    // rows 0..31: forward substitution with the top-left triangle
+    T b0[32];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) b[i] = (i < m) ? B[(long)i * ldb + col] : T(0);
+    for (int i = 0; i < 32; ++i) b0[i] = (i < m) ? B[(long)i * ldb + col] : T(0);
 #pragma unroll
-    for (int i = 1; i < 64; ++i) {
-        T s = b[i];
+    for (int i = 1; i < 32; ++i) {
+        T s = b0[i];
 #pragma unroll
-        for (int l = 0; l < i; ++l) s = fma(-Ls[i][l], b[l], s);
-        b[i] = s;
+        for (int l = 0; l < i; ++l) s = fma(-Ls[i][l], b0[l], s);
+        b0[i] = s;
     }
 #pragma unroll
-    for (int i = 0; i < 64; ++i)
-        if (i < m) B[(long)i * ldb + col] = b[i];
+    for (int i = 0; i < 32; ++i)
+        if (i < m) B[(long)i * ldb + col] = b0[i];
+    if (m <= 32) return;
+    // rows 32..63: subtract the off-diagonal block, then the bottom-right triangle
+    T b1[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        T s = (32 + i < m) ? B[(long)(32 + i) * ldb + col] : T(0);
+#pragma unroll
+        for (int l = 0; l < 32; ++l) s = fma(-Ls[32 + i][l], b0[l], s);
+        b1[i] = s;
+    }
+#pragma unroll
+    for (int i = 1; i < 32; ++i) {
+        T s = b1[i];
+#pragma unroll
+        for (int l = 0; l < i; ++l) s = fma(-Ls[32 + i][32 + l], b1[l], s);
+        b1[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (32 + i < m) B[(long)(32 + i) * ldb + col] = b1[i];
 }
 
 }  // namespace

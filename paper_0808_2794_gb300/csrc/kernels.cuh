@@ -36,6 +36,12 @@ cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs,
 template <typename T>
 cudaError_t launch_gemm_sub(int M, int N, int K, const T *A, long lda, const T *B, long ldb,
                             T *C, long ldc, cudaStream_t s);
+// Batched C_z = beta*C_z + alpha*A_z*B_z (beta = 0 or 1), z = 0..batch-1,
+// with X_z = X + (z / inner) * x_outer + (z % inner) * x_inner.
+template <typename T>
+cudaError_t launch_gemm_batched(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,
+                                T *C, long ldc, int batch, int inner, long a_outer, long a_inner, long b_outer,
+                                long b_inner, long c_outer, long c_inner, cudaStream_t s);
 // B[m x N] <- L^{-1} B with L unit lower (m x m, ldl), m <= 64.
 template <typename T>
 cudaError_t launch_trsm_llnu_small(int m, int N, const T *L, long ldl, T *B, long ldb,
@@ -50,30 +56,32 @@ cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, 
 cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s);
 
 // ---- triangular solves with the factors (trsv.cu) ---------------------------
-// Block size of the blocked solves: 128 rows (FP32), 64 rows (FP64).
-template <typename T> int trsv_block_size();
-// Bytes of the per-chunk partial-sum slots for order n, block size bs.
-size_t trsv_slot_bytes(int n, int bs, size_t elem);
+// Diagonal blocks of L and U are inverted at block size BI (1024 rows FP32,
+// 512 FP64, smaller for small n); the solves then take n/BI steps.
+template <typename T> int trsv_inverse_block(int n);
+template <typename T> size_t trsv_inverse_bytes(int n);  // per triangle
+template <typename T> size_t trsv_tmp_bytes(int n);
 template <typename T>
-cudaError_t launch_diag_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, cudaStream_t s);
-// Lower solve: Y[:,c] = L^{-1} (P r_c) / s_c, r FP64 col-major (ldr), perm the
-// row permutation, s_c = 2^ceil(log2 rnorm[c]).  flags/counts: one int per
-// block (zero before the first epoch), ticket: one int; epoch = 1, 2, ...
+cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s);
+// Lower solve: Y[:,c] = L^{-1} (P r_c) / s_c with r FP64 col-major (ldr), perm
+// the row permutation, s_c = 2^ceil(log2 rnorm[c]).  acc: n*nrhs scratch of T;
+// bar: two unsigned words, zero before first use (a grid barrier).
 template <typename T>
 cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv, const double *R, long ldr,
-                              const int *perm, const double *rnorm, T *Y, long ldy, T *slots, int *flags,
-                              int *counts, int *ticket, int epoch, MpDevStatus *st, cudaStream_t s);
+                              const int *perm, const double *rnorm, T *Y, long ldy, T *acc, unsigned *bar,
+                              MpDevStatus *st, cudaStream_t s);
+// Upper solve: Z = U^{-1} Y.
 template <typename T>
 cudaError_t launch_trsv_upper(int n, int nrhs, const T *W, long ldw, const T *Uinv, const T *Y, long ldy, T *Z,
-                              long ldz, T *slots, int *flags, int *counts, int *ticket, int epoch,
-                              MpDevStatus *st, cudaStream_t s);
+                              long ldz, T *acc, unsigned *bar, MpDevStatus *st, cudaStream_t s);
 
 // ---- FP64 residual and update (refine.cu) -----------------------------------
 int residual_ksplit(int n, int nrhs);
 // part[ks][c][i] partial sums of (A X)[i,c] over column chunk ks.
 cudaError_t launch_residual_partial(int n, int nrhs, const double *A, long lda, const double *X,
                                     long ldx, double *part, int ksplit, cudaStream_t s);
-// R = B - sum_ks part; rnorm[c] = ||R_c||inf, xnorm[c] = ||X_c||inf (zeroed first).
+// R = B - sum_ks part (R = A X when B is null); rnorm[c] = ||R_c||inf,
+// xnorm[c] = ||X_c||inf (zeroed first).
 cudaError_t launch_residual_finalize(int n, int nrhs, const double *part, int ksplit,
                                      const double *B, long ldb, const double *X, long ldx,
                                      double *R, long ldr, double *rnorm, double *xnorm,
@@ -85,3 +93,14 @@ cudaError_t launch_update(int n, int nrhs, const T *Z, long ldz, const double *r
 // bnorm[c] = ||B_c||_inf (zeroed first)
 cudaError_t launch_col_absmax(int n, int nrhs, const double *B, long ldb, double *out,
                               MpDevStatus *st, cudaStream_t s);
+
+// ---- GMRES-based refinement pieces (refine.cu) -------------------------------
+// out[j] = V[:, j] . w for j < k (FP64, column-major V)
+cudaError_t launch_dots(int n, int k, const double *V, long ldv, const double *w, double *out, cudaStream_t s);
+// w -= V[:, 0:k] h
+cudaError_t launch_project(int n, int k, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
+// x += Z[:, 0:k] y; *znorm = max |Z y| (zeroed first)
+cudaError_t launch_correct(int n, int k, const double *Z, long ldz, const double *y, double *x, double *znorm,
+                           cudaStream_t s);
+// dst = src / *alpha_inv
+cudaError_t launch_scale(int n, const double *src, const double *alpha_inv, double *dst, cudaStream_t s);

@@ -24,6 +24,7 @@
 // the composed row permutation as (destination, source) moves for the row
 // exchange of the rest of the matrix.
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -36,29 +37,65 @@ __device__ __forceinline__ T mag(T v) {
     return (a != a) ? T(INFINITY) : a;  // NaN -> +inf
 }
 
-template <typename T>
-__device__ __forceinline__ void better(T &bv, int &bi, int &bw, T ov, int oi, int ow) {
-    if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-        bw = ow;
+// Pivot candidate: magnitude and row, ordered by magnitude, ties to the
+// smaller row.  FP32 packs both into one 64-bit key (non-negative float bits
+// order like unsigned integers), so a warp reduction is one 64-bit shuffle
+// per round.  "No candidate" is the smallest key.
+template <typename T> struct Cand;
+template <> struct Cand<float> {
+    unsigned long long k;
+    __device__ __forceinline__ static Cand none() { return Cand{0ull}; }
+    __device__ __forceinline__ static Cand make(float m, int idx) {
+        return Cand{((unsigned long long)__float_as_uint(m) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)idx)};
     }
+    __device__ __forceinline__ bool better(const Cand &o) const { return k > o.k; }
+    __device__ __forceinline__ int idx() const { return k == 0ull ? INT_MAX : (int)(0xFFFFFFFFu - (unsigned)k); }
+    __device__ __forceinline__ Cand shfl_xor(int off) const { return Cand{__shfl_xor_sync(0xffffffffu, k, off)}; }
+    __device__ __forceinline__ static Cand load_remote(uint32_t addr) {
+        unsigned long long v;
+        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+        return Cand{v};
+    }
+};
+template <> struct Cand<double> {
+    double v;
+    int i;
+    __device__ __forceinline__ static Cand none() { return Cand{-1.0, INT_MAX}; }
+    __device__ __forceinline__ static Cand make(double m, int idx) { return Cand{m, idx}; }
+    __device__ __forceinline__ bool better(const Cand &o) const { return v > o.v || (v == o.v && i < o.i); }
+    __device__ __forceinline__ int idx() const { return i; }
+    __device__ __forceinline__ Cand shfl_xor(int off) const {
+        return Cand{__shfl_xor_sync(0xffffffffu, v, off), __shfl_xor_sync(0xffffffffu, i, off)};
+    }
+    __device__ __forceinline__ static Cand load_remote(uint32_t addr) {
+        return Cand{ld_dsmem_f64(addr), ld_dsmem_s32(addr + 8)};
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ Cand<T> warp_best(Cand<T> c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Cand<T> o = c.shfl_xor(off);
+        if (o.better(c)) c = o;
+    }
+    return c;
 }
 
 template <typename T, int NB, int NT, int RPT>
 struct PanelSmem {
-    T fin[NT * RPT][NB];     // finished values of the local rows (natural column order)
-    T wrow[2][NT / 32][NB];  // per-warp candidate rows
-    T drow[2][NB];           // diagonal row
-    T prow[NT / 32][2 * NB]; // per-warp copy of the pivot row (padded)
-    T orow[NT / 32][NB];     // per-warp copy of the old diagonal row
-    T wval[2][NT / 32];
-    int widx[2][NT / 32];
-    int worig[2][NT / 32];
+    T fin[NT * RPT][NB + 1];        // finished values of the local rows (natural column order;
+                                    // odd row stride: consecutive rows fall in different banks)
+    T crow[2][NB];                  // this CTA's candidate row (double-buffered: read remotely)
+    T drow[2][NB];                  // the diagonal row, if this CTA holds it
+    __align__(16) T prow_s[2 * NB]; // pivot row in shifted coordinates: prow_s[t] = pivot[j + t]
+    T prow[NB];                     // pivot row, natural columns
+    T orow[NB];                     // old diagonal row, natural columns
+    Cand<T> wkey[NT / 32];
+    Cand<T> ckey[2];
+    int corig[2];
     int dorig[2];
-    T cval[2];
-    int cidx[2];
-    int cwarp[2];
+    int cidx, p, porig, dorg;
 };
 
 template <typename T, int NB, int RPT, int NT>
@@ -67,6 +104,8 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                    int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<PanelSmem<T, NB, NT, RPT> *>(smem_raw);
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T);
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int CL = (int)cluster_nctarank();
@@ -74,6 +113,7 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
     const int rpc = (m + CL - 1) / CL;
     const int rbase = rank * rpc;
     if (rank == 0 && tid == 0) *nmoves = 0;
+    for (int t = tid; t < 2 * NB; t += NT) sm.prow_s[t] = T(0);
 
     T a[RPT][NB];
     int gi[RPT], orig[RPT];
@@ -92,118 +132,112 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
     int buf = 0;
 #pragma unroll 1
     for (int j = 0; j < NB; ++j) {
-        const bool live = j < ncols;  // uniform: dead steps only shift
-        int p = -1;
-        if (live) {
-            __syncwarp();  // retired values of the previous column are visible to the warp
-            // ---- 1. candidates
-            T bv = T(-1);
-            int bi = INT_MAX, bo = -1, bs = -1;
+        if (j < ncols) {  // uniform: dead steps only shift
+            // ---- 1. warp candidates
+            Cand<T> c = Cand<T>::none();
 #pragma unroll
             for (int s = 0; s < RPT; ++s)
                 if (gi[s] >= j && gi[s] < m) {
-                    const T v = mag(a[s][0]);
-                    if (v > bv) { bv = v; bi = gi[s]; bo = orig[s]; bs = s; }
+                    const Cand<T> o = Cand<T>::make(mag(a[s][0]), gi[s]);
+                    if (o.better(c)) c = o;
                 }
-            T wv = bv;
-            int wi = bi, wl = lane;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ov = __shfl_xor_sync(0xffffffffu, wv, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
-                const int ol = __shfl_xor_sync(0xffffffffu, wl, off);
-                better(wv, wi, wl, ov, oi, ol);
-            }
-            // the winning lane publishes its row: finished part from shared
-            // memory (copied by the whole warp), active part from registers
-            const int ws_ = __shfl_sync(0xffffffffu, bs, wl);
-            if (wi != INT_MAX) {
-                const int lrow = (warp * 32 + wl) + ws_ * NT;
-                for (int k = lane; k < j; k += 32) sm.wrow[buf][warp][k] = sm.fin[lrow][k];
-                if (lane == wl) {
-#pragma unroll
-                    for (int s = 0; s < RPT; ++s)
-                        if (s == bs) {
-#pragma unroll
-                            for (int t = 0; t < NB; ++t)
-                                if (j + t < NB) sm.wrow[buf][warp][j + t] = a[s][t];
-                        }
-                    sm.wval[buf][warp] = bv;
-                    sm.widx[buf][warp] = bi;
-                    sm.worig[buf][warp] = bo;
-                }
-            } else if (lane == 0) {
-                sm.wval[buf][warp] = T(-1);
-                sm.widx[buf][warp] = INT_MAX;
-            }
-            // the diagonal row j
-#pragma unroll
-            for (int s = 0; s < RPT; ++s)
-                if (gi[s] == j) {
-                    const int lrow = tid + s * NT;
-                    for (int k = 0; k < j; ++k) sm.drow[buf][k] = sm.fin[lrow][k];
-#pragma unroll
-                    for (int t = 0; t < NB; ++t)
-                        if (j + t < NB) sm.drow[buf][j + t] = a[s][t];
-                    sm.dorig[buf] = orig[s];
-                }
+            c = warp_best(c);
+            if (lane == 0) sm.wkey[warp] = c;
             __syncthreads();
-            // ---- 2. CTA candidate
+            // ---- 2. the CTA candidate (warp 0)
             if (warp == 0) {
-                T v = lane < NW ? sm.wval[buf][lane] : T(-1);
-                int i = lane < NW ? sm.widx[buf][lane] : INT_MAX;
-                int w = lane;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const T ov = __shfl_xor_sync(0xffffffffu, v, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, i, off);
-                    const int ow = __shfl_xor_sync(0xffffffffu, w, off);
-                    better(v, i, w, ov, oi, ow);
+                Cand<T> cc = lane < NW ? sm.wkey[lane] : Cand<T>::none();
+                cc = warp_best(cc);
+                if (lane == 0) {
+                    sm.ckey[buf] = cc;
+                    sm.cidx = cc.idx();
                 }
-                if (lane == 0) { sm.cval[buf] = v; sm.cidx[buf] = i; sm.cwarp[buf] = w; }
+            }
+            __syncthreads();
+            // ---- 3. publish the CTA candidate row and the diagonal row (only the
+            //         warps that hold them take the branch)
+            const int ci = sm.cidx;
+            bool mine_c = false, mine_d = false;
+#pragma unroll
+            for (int s = 0; s < RPT; ++s) {
+                mine_c |= gi[s] == ci;
+                mine_d |= gi[s] == j;
+            }
+            if (__any_sync(0xffffffffu, mine_c || mine_d)) {
+#pragma unroll
+                for (int s = 0; s < RPT; ++s) {
+                    if (gi[s] == ci) {
+                        const int lrow = tid + s * NT;
+                        for (int k = 0; k < j; ++k) sm.crow[buf][k] = sm.fin[lrow][k];
+#pragma unroll
+                        for (int t = 0; t < NB; ++t)
+                            if (j + t < NB) sm.crow[buf][j + t] = a[s][t];
+                        sm.corig[buf] = orig[s];
+                    }
+                    if (gi[s] == j) {
+                        const int lrow = tid + s * NT;
+                        for (int k = 0; k < j; ++k) sm.drow[buf][k] = sm.fin[lrow][k];
+#pragma unroll
+                        for (int t = 0; t < NB; ++t)
+                            if (j + t < NB) sm.drow[buf][j + t] = a[s][t];
+                        sm.dorig[buf] = orig[s];
+                    }
+                }
             }
             if (CL > 1) cluster_sync_all(); else __syncthreads();
-            // ---- 3. every warp reads the cluster's candidates
-            T v = T(-1);
-            int i = INT_MAX, w = 0, rk = lane;
-            if (lane < CL) {
-                if (CL > 1) {
-                    v = ld_dsmem<T>(mapa_shared(smem_u32(&sm.cval[buf]), lane));
-                    i = ld_dsmem_s32(mapa_shared(smem_u32(&sm.cidx[buf]), lane));
-                    w = ld_dsmem_s32(mapa_shared(smem_u32(&sm.cwarp[buf]), lane));
-                } else {
-                    v = sm.cval[buf]; i = sm.cidx[buf]; w = sm.cwarp[buf];
-                }
-            }
-            int wpack = w * 32 + rk;
+            // ---- 4. warp 0 reads the cluster's candidates and fetches the rows
+            if (warp == 0) {
+                Cand<T> g = Cand<T>::none();
+                if (lane < CL) g = (CL > 1) ? Cand<T>::load_remote(mapa_shared(smem_u32(&sm.ckey[buf]), lane))
+                                            : sm.ckey[buf];
+                g = warp_best(g);
+                const int p = g.idx();
+                const int wr = p / rpc;  // CTA holding the pivot row
+                const int dr = j / rpc;  // CTA holding the diagonal row
+                // issue every remote load before using any of them
+                T pv[(NB + 31) / 32], ov[(NB + 31) / 32];
+                int po = 0, dor = 0;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ov = __shfl_xor_sync(0xffffffffu, v, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, i, off);
-                const int ow = __shfl_xor_sync(0xffffffffu, wpack, off);
-                better(v, i, wpack, ov, oi, ow);
-            }
-            p = i;
-            const int wr = wpack & 31, ww = wpack >> 5;  // CTA and warp slot of the pivot row
-            const int dr = j / rpc;                      // CTA holding the diagonal row
-            int porig, dorig;
-            if (CL > 1) {
-                for (int k = lane; k < NB; k += 32) {
-                    sm.prow[warp][k] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.wrow[buf][ww][k]), wr));
-                    sm.orow[warp][k] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.drow[buf][k]), dr));
+                for (int q = 0; q < (NB + 31) / 32; ++q) {
+                    const int k = lane + 32 * q;
+                    if (k < NB) {
+                        if (CL > 1) {
+                            pv[q] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.crow[buf][k]), wr));
+                            ov[q] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.drow[buf][k]), dr));
+                        } else {
+                            pv[q] = sm.crow[buf][k];
+                            ov[q] = sm.drow[buf][k];
+                        }
+                    }
                 }
-                porig = ld_dsmem_s32(mapa_shared(smem_u32(&sm.worig[buf][ww]), wr));
-                dorig = ld_dsmem_s32(mapa_shared(smem_u32(&sm.dorig[buf]), dr));
-            } else {
-                for (int k = lane; k < NB; k += 32) {
-                    sm.prow[warp][k] = sm.wrow[buf][ww][k];
-                    sm.orow[warp][k] = sm.drow[buf][k];
+                if (lane == 0) {
+                    if (CL > 1) {
+                        po = ld_dsmem_s32(mapa_shared(smem_u32(&sm.corig[buf]), wr));
+                        dor = ld_dsmem_s32(mapa_shared(smem_u32(&sm.dorig[buf]), dr));
+                    } else {
+                        po = sm.corig[buf];
+                        dor = sm.dorig[buf];
+                    }
                 }
-                porig = sm.worig[buf][ww];
-                dorig = sm.dorig[buf];
+#pragma unroll
+                for (int q = 0; q < (NB + 31) / 32; ++q) {
+                    const int k = lane + 32 * q;
+                    if (k < NB) {
+                        sm.prow[k] = pv[q];
+                        sm.orow[k] = ov[q];
+                        sm.prow_s[k - j + NB] = T(0);  // clear the tail left by earlier columns
+                        if (k >= j) sm.prow_s[k - j] = pv[q];
+                    }
+                }
+                if (lane == 0) {
+                    sm.p = p;
+                    sm.porig = po;
+                    sm.dorg = dor;
+                }
             }
-            __syncwarp();
-            const T piv = sm.prow[warp][j];
+            __syncthreads();
+            const int p = sm.p;
+            const T piv = sm.prow[j];
             if (rank == 0 && tid == 0) {
                 ipiv[j] = row0 + p + 1;
                 if (piv == T(0)) {
@@ -213,18 +247,24 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     mp_flag(st, MP_FLAG_LOWP_BREAKDOWN);
                 }
             }
-            // ---- row exchange (finished part in shared memory, active part in registers)
+            // ---- 5. row exchange (finished part in shared memory, active part in
+            //         registers); only the warps holding row p or row j branch
+            bool mine_x = false;
 #pragma unroll
-            for (int s = 0; s < RPT; ++s) {
-                const bool is_p = gi[s] == p && p != j;
-                const bool is_j = gi[s] == j;
-                if (is_p || is_j) {
-                    const T *src = is_p ? sm.orow[warp] : sm.prow[warp];
-                    const int lrow = tid + s * NT;
-                    for (int k = 0; k < j; ++k) sm.fin[lrow][k] = src[k];
+            for (int s = 0; s < RPT; ++s) mine_x |= (gi[s] == p && p != j) || gi[s] == j;
+            if (__any_sync(0xffffffffu, mine_x)) {
 #pragma unroll
-                    for (int t = 0; t < NB; ++t) a[s][t] = (j + t < NB) ? src[j + t] : T(0);
-                    orig[s] = is_p ? dorig : porig;
+                for (int s = 0; s < RPT; ++s) {
+                    const bool is_p = gi[s] == p && p != j;
+                    const bool is_j = gi[s] == j;
+                    if (is_p || is_j) {
+                        const T *src = is_p ? sm.orow : sm.prow;
+                        const int lrow = tid + s * NT;
+                        for (int k = 0; k < j; ++k) sm.fin[lrow][k] = src[k];
+#pragma unroll
+                        for (int t = 0; t < NB; ++t) a[s][t] = (j + t < NB) ? src[j + t] : T(0);
+                        orig[s] = is_p ? sm.dorg : sm.porig;
+                    }
                 }
             }
             // ---- scale and rank-1 update of the active columns
@@ -238,12 +278,19 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     a[s][0] = l[s];
                 }
             }
-            const T *prw = sm.prow[warp] + j;
+            const V *pr4 = reinterpret_cast<const V *>(sm.prow_s);
 #pragma unroll
-            for (int t = 1; t < NB; ++t) {
-                const T pv = prw[t];
+            for (int q = 0; q < NB / VW; ++q) {
+                const V v4 = pr4[q];
+                const T *pv = reinterpret_cast<const T *>(&v4);
 #pragma unroll
-                for (int s = 0; s < RPT; ++s) a[s][t] = fma(-l[s], pv, a[s][t]);
+                for (int e = 0; e < VW; ++e) {
+                    const int t = q * VW + e;
+                    if (t >= 1) {
+#pragma unroll
+                        for (int s = 0; s < RPT; ++s) a[s][t] = fma(-l[s], pv[e], a[s][t]);
+                    }
+                }
             }
         }
         // ---- retire column j and shift the active columns
@@ -256,7 +303,7 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
         }
         buf ^= 1;
     }
-    __syncwarp();
+    __syncthreads();
     // write back the finished rows and the composed permutation
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {

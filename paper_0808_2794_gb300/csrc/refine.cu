@@ -78,7 +78,7 @@ residual_finalize_kernel(int n, int nrhs, const double *__restrict__ part, int k
     if (row < n) {
         double s = 0.0;
         for (int ks = 0; ks < ksplit; ++ks) s += part[((long)ks * nrhs + c) * n + row];
-        const double r = B[(long)c * ldb + row] - s;
+        const double r = B ? B[(long)c * ldb + row] - s : s;  // B == nullptr: R = A X
         R[(long)c * ldr + row] = r;
         rv = fabs(r);
         xv = fabs(X[(long)c * ldx + row]);
@@ -198,5 +198,95 @@ cudaError_t launch_col_absmax(int n, int nrhs, const double *B, long ldb, double
     dim3 grid((n + 255) / 256, nrhs);
     mp_note_launch();
     col_absmax_kernel<<<grid, 256, 0, s>>>(n, B, ldb, out, st);
+    return cudaGetLastError();
+}
+
+// ============================================================================
+// Building blocks of GMRES-based refinement (Section 2.2: a Krylov method on
+// A d = r, right-preconditioned by M = (LU)^{-1} P; Section 4): FP64 dot
+// products against the Krylov basis, projection, 2-norms, and the correction
+// x += Z y.  Deterministic: every reduction has a fixed order.
+// ============================================================================
+namespace {
+
+// out[j] = sum_i V[i, j] w[i] for j < k; one CTA per column.
+__global__ void __launch_bounds__(1024)
+dots_kernel(int n, const double *__restrict__ V, long ldv, const double *__restrict__ w, double *out) {
+    __shared__ double red[32];
+    const int j = blockIdx.x;
+    const double *v = V + (long)j * ldv;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(v[i], w[i], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) out[j] = s;
+    }
+}
+
+// w[i] -= sum_{j<k} V[i, j] h[j]
+__global__ void __launch_bounds__(256)
+project_kernel(int n, int k, const double *__restrict__ V, long ldv, const double *__restrict__ h, double *w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = w[i];
+    for (int j = 0; j < k; ++j) s = fma(-V[(long)j * ldv + i], h[j], s);
+    w[i] = s;
+}
+
+// x[i] += sum_{j<k} Z[i, j] y[j]; znorm = max |sum| (atomic, zeroed first)
+__global__ void __launch_bounds__(256)
+correct_kernel(int n, int k, const double *__restrict__ Z, long ldz, const double *__restrict__ y, double *x,
+               double *znorm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0.0;
+    if (i < n) {
+        for (int j = 0; j < k; ++j) d = fma(Z[(long)j * ldz + i], y[j], d);
+        x[i] += d;
+    }
+    double a = fabs(d);
+    if (a != a) a = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(znorm, a);
+}
+
+// dst = src * alpha (alpha read from device memory, as 1/alpha_inv)
+__global__ void __launch_bounds__(256)
+scale_kernel(int n, const double *__restrict__ src, const double *__restrict__ alpha_inv, double *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] / *alpha_inv;
+}
+
+}  // namespace
+
+cudaError_t launch_dots(int n, int k, const double *V, long ldv, const double *w, double *out, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    mp_note_launch();
+    dots_kernel<<<k, 1024, 0, s>>>(n, V, ldv, w, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_project(int n, int k, const double *V, long ldv, const double *h, double *w, cudaStream_t s) {
+    if (k <= 0 || n <= 0) return cudaSuccess;
+    mp_note_launch();
+    project_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, k, V, ldv, h, w);
+    return cudaGetLastError();
+}
+cudaError_t launch_correct(int n, int k, const double *Z, long ldz, const double *y, double *x, double *znorm,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    mp_note_launch();
+    correct_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, k, Z, ldz, y, x, znorm);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale(int n, const double *src, const double *alpha_inv, double *dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    mp_note_launch();
+    scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, src, alpha_inv, dst);
     return cudaGetLastError();
 }

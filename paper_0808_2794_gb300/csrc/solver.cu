@@ -144,8 +144,8 @@ int outer_nb(int n, const mp_opts &o) {
 // workspace layout
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, flagsL, flagsU,
-        countsL, countsU, slots, tickets, R, Y, Z, part, tc, total;
+    size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, R, Y, Z,
+        part, tc, total;
     size_t W_bytes;
     int ldw, nblk, ksplit, nb;
 };
@@ -176,22 +176,19 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, L.nb));
     L.npairs = carve(off, sizeof(int) * 4);
     L.map = carve(off, sizeof(int) * (size_t)n);
-    const size_t inv_bytes = std::max((size_t)((n + 127) / 128) * 128 * 128 * sizeof(float),
-                                      fp64_space ? (size_t)L.nblk * 64 * 64 * sizeof(double) : 0);
+    const size_t inv_bytes = std::max(trsv_inverse_bytes<float>(n), fp64_space ? trsv_inverse_bytes<double>(n) : 0);
     L.Linv = carve(off, inv_bytes);
     L.Uinv = carve(off, inv_bytes);
-    L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.countsL = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.countsU = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.slots = carve(off, std::max(trsv_slot_bytes(n, 128, sizeof(float)),
-                                  fp64_space ? trsv_slot_bytes(n, 64, sizeof(double)) : 0));
-    L.tickets = carve(off, sizeof(int) * 4);
+    L.invtmp = carve(off, std::max(trsv_tmp_bytes<float>(n), fp64_space ? trsv_tmp_bytes<double>(n) : 0));
+    L.acc = carve(off, el * (size_t)n * rhs);
+    L.bar = carve(off, sizeof(unsigned) * 4);
     L.R = carve(off, sizeof(double) * (size_t)n * rhs);
     L.Y = carve(off, el * (size_t)n * rhs);
     L.Z = carve(off, el * (size_t)n * rhs);
     L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
-    L.tc = carve(off, tc_workspace_bytes(n, L.nb, o.prec));
+    L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
+                                             : std::max(tc_workspace_bytes(n, L.nb, o.prec),
+                                                        tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
     L.total = align_up(off, 256);
     return L;
 }
@@ -237,15 +234,30 @@ struct FactorCtx {
         if (_e != cudaSuccess) return _e;             \
     } while (0)
 
+// C -= A B for the FP32-accurate updates inside the panel and the triangular
+// solve: plain FP32 FMA for the FP32 rung (and in FP64 for the fallback),
+// the split-fp16 tensor-core product (about FP32 accuracy) for the tensor-core
+// rungs, once the product is large enough to fill the machine.
+template <typename T>
+cudaError_t gemm_fp32_accurate(FactorCtx<T> &c, int M, int N, int K, const T *A, long lda, const T *B, long ldb,
+                               T *C, long ldc) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (sizeof(T) == 4 && c.prec != MP_PREC_FP32 && (double)M * N * K >= 1.0e8 && lda % 4 == 0 && ldb % 4 == 0)
+        return tc_trailing_update(MP_PREC_FP16X3, M, N, K, reinterpret_cast<const float *>(A), lda,
+                                  reinterpret_cast<const float *>(B), ldb, reinterpret_cast<float *>(C), ldc, c.tc,
+                                  c.st, c.s);
+    return launch_gemm_sub<T>(M, N, K, A, lda, B, ldb, C, ldc, c.s);
+}
+
 // B <- L^{-1} B, L unit lower m x m (recursive: small base solve + GEMM update).
 template <typename T>
-cudaError_t trsm_rec(int m, int N, const T *L, long ldl, T *B, long ldb, cudaStream_t s) {
+cudaError_t trsm_rec(FactorCtx<T> &c, int m, int N, const T *L, long ldl, T *B, long ldb) {
     if (m <= 0 || N <= 0) return cudaSuccess;
-    if (m <= 64) return launch_trsm_llnu_small<T>(m, N, L, ldl, B, ldb, s);
+    if (m <= 64) return launch_trsm_llnu_small<T>(m, N, L, ldl, B, ldb, c.s);
     const int m1 = (m / 2 + 31) / 32 * 32;
-    CU(trsm_rec<T>(m1, N, L, ldl, B, ldb, s));
-    CU(launch_gemm_sub<T>(m - m1, N, m1, L + (long)m1 * ldl, ldl, B, ldb, B + (long)m1 * ldb, ldb, s));
-    return trsm_rec<T>(m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb, s);
+    CU(trsm_rec<T>(c, m1, N, L, ldl, B, ldb));
+    CU(gemm_fp32_accurate<T>(c, m - m1, N, m1, L + (long)m1 * ldl, ldl, B, ldb, B + (long)m1 * ldb, ldb));
+    return trsm_rec<T>(c, m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb);
 }
 
 // Recursive LU of the columns [k0, k0+ncols) of rows [k0, n) (a recursive
@@ -273,9 +285,9 @@ cudaError_t getrf_rec(FactorCtx<T> &c, int k0, int ncols) {
     CU(getrf_rec<T>(c, k0, n1));
     {
         MpProfScope ps(MP_KC_PANELGEMM, (double)n1 * n1 * (ncols - n1) + 2.0 * (m - n1) * (ncols - n1) * n1, c.s);
-        CU(trsm_rec<T>(n1, ncols - n1, W + (long)k0 * ld + k0, ld, W + (long)k0 * ld + k0 + n1, ld, c.s));
-        CU(launch_gemm_sub<T>(m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
-                              W + (long)k0 * ld + k0 + n1, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld, c.s));
+        CU(trsm_rec<T>(c, n1, ncols - n1, W + (long)k0 * ld + k0, ld, W + (long)k0 * ld + k0 + n1, ld));
+        CU(gemm_fp32_accurate<T>(c, m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
+                                 W + (long)k0 * ld + k0 + n1, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld));
     }
     return getrf_rec<T>(c, k0 + n1, ncols - n1);
 }
@@ -295,7 +307,7 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
         if (rest > 0) {
             {
                 MpProfScope ps(MP_KC_TRSM, (double)nbk * nbk * rest, c.s);
-                CU(trsm_rec<T>(nbk, rest, W + (long)k * ld + k, ld, W + (long)k * ld + k + nbk, ld, c.s));
+                CU(trsm_rec<T>(c, nbk, rest, W + (long)k * ld + k, ld, W + (long)k * ld + k + nbk, ld));
             }
             MpProfScope ps(MP_KC_UPDATE, 2.0 * rest * rest * nbk, c.s);
             const T *L21 = W + (long)(k + nbk) * ld + k;
@@ -346,13 +358,10 @@ int lowp_solve(Solve &S, const double *R, long ldr, const double *rnorm) {
     MpProfScope ps(MP_KC_TRSV, (double)S.n * S.n * sizeof(T) + 4.0 * S.n * S.nrhs * sizeof(T), S.s);
     MP_CUDA_TRY(launch_trsv_lower<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Linv), R, ldr,
                                      at<int>(S.work, L.perm), rnorm, at<T>(S.work, L.Y), S.n,
-                                     at<T>(S.work, L.slots), at<int>(S.work, L.flagsL),
-                                     at<int>(S.work, L.countsL), at<int>(S.work, L.tickets), S.epoch,
-                                     &S.sb->st, S.s));
+                                     at<T>(S.work, L.acc), at<unsigned>(S.work, L.bar), &S.sb->st, S.s));
     MP_CUDA_TRY(launch_trsv_upper<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Uinv), at<T>(S.work, L.Y),
-                                     S.n, at<T>(S.work, L.Z), S.n, at<T>(S.work, L.slots),
-                                     at<int>(S.work, L.flagsU), at<int>(S.work, L.countsU),
-                                     at<int>(S.work, L.tickets) + 1, S.epoch, &S.sb->st, S.s));
+                                     S.n, at<T>(S.work, L.Z), S.n, at<T>(S.work, L.acc),
+                                     at<unsigned>(S.work, L.bar), &S.sb->st, S.s));
     return 0;
 }
 
@@ -368,14 +377,9 @@ int residual(Solve &S) {
     return 0;
 }
 
-// Resets the per-solve flags/tickets (epoch restarts at 0).
+// Resets the grid-barrier words of the triangular solves.
 int reset_sync(Solve &S) {
-    const Layout &L = S.L;
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsL), 0, sizeof(int) * L.nblk, S.s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.flagsU), 0, sizeof(int) * L.nblk, S.s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.countsL), 0, sizeof(int) * L.nblk, S.s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.countsU), 0, sizeof(int) * L.nblk, S.s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(S.work, L.tickets), 0, sizeof(int) * 4, S.s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<unsigned>(S.work, S.L.bar), 0, sizeof(unsigned) * 4, S.s));
     S.epoch = 0;
     return 0;
 }
@@ -392,7 +396,8 @@ int factor(Solve &S, int prec, int nb, int *info_out, uint32_t *flags_out) {
                    at<int2>(S.work, L.pairs), at<int>(S.work, L.npairs), at<int>(S.work, L.map),
                    &S.sb->st, S.s, prec, at<void>(S.work, L.tc)};
     MP_CUDA_TRY(getrf_blocked<T>(c, nb));
-    MP_CUDA_TRY(launch_diag_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv), S.s));
+    MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
+                                         at<T>(S.work, L.invtmp), S.s));
     StatusBlock h;
     int e = read_status(S, h);
     if (e) return e;
@@ -648,8 +653,7 @@ extern "C" int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const do
 // ---------------------------------------------------------------------------
 namespace {
 struct StepLayout {
-    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, flagsL, flagsU, countsL, countsU, slots,
-        tickets, Y, Z, part, tc, total;
+    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, Y, Z, part, tc, total;
     int nblk, ksplit;
 };
 StepLayout step_layout(int n, int nrhs, int nb, int prec) {
@@ -664,18 +668,17 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, nb));
     L.npairs = carve(off, sizeof(int) * 4);
     L.map = carve(off, sizeof(int) * (size_t)n);
-    L.Linv = carve(off, sizeof(float) * (size_t)L.nblk * 128 * 128);
-    L.Uinv = carve(off, sizeof(float) * (size_t)L.nblk * 128 * 128);
-    L.flagsL = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.flagsU = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.countsL = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.countsU = carve(off, sizeof(int) * (size_t)L.nblk);
-    L.slots = carve(off, trsv_slot_bytes(n, 128, sizeof(float)));
-    L.tickets = carve(off, sizeof(int) * 4);
+    L.Linv = carve(off, trsv_inverse_bytes<float>(n));
+    L.Uinv = carve(off, trsv_inverse_bytes<float>(n));
+    L.invtmp = carve(off, trsv_tmp_bytes<float>(n));
+    L.acc = carve(off, sizeof(float) * (size_t)n * rhs);
+    L.bar = carve(off, sizeof(unsigned) * 4);
     L.Y = carve(off, sizeof(float) * (size_t)n * rhs);
     L.Z = carve(off, sizeof(float) * (size_t)n * rhs);
     L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
-    L.tc = carve(off, tc_workspace_bytes(n, nb, prec));
+    L.tc = carve(off, prec == MP_PREC_FP32 ? 0
+                                           : std::max(tc_workspace_bytes(n, nb, prec),
+                                                      tc_workspace_bytes(n, nb, MP_PREC_FP16X3)));
     L.total = align_up(off, 256);
     return L;
 }
@@ -760,7 +763,7 @@ extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const in
     if (n < 0) return mp_arg_fail(1, "n < 0");
     if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
     if (n > 0 && !dW) return mp_arg_fail(3, "W is NULL");
-    if (ldw < std::max(1, n)) return mp_arg_fail(4, "ldw < max(1, n)");
+    if (ldw < std::max(1, n) || ldw % 4) return mp_arg_fail(4, "ldw must be >= n and a multiple of 4");
     if (n > 0 && !dipiv) return mp_arg_fail(5, "ipiv is NULL");
     if (n > 0 && nrhs > 0 && !dR) return mp_arg_fail(6, "R is NULL");
     if (ldr < std::max(1, n)) return mp_arg_fail(7, "ldr < max(1, n)");
@@ -773,11 +776,7 @@ extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     StatusBlock *sb = at<StatusBlock>(work, L.status);
     MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsL), 0, sizeof(int) * L.nblk, s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.flagsU), 0, sizeof(int) * L.nblk, s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.countsL), 0, sizeof(int) * L.nblk, s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.countsU), 0, sizeof(int) * L.nblk, s));
-    MP_CUDA_TRY(cudaMemsetAsync(at<int>(work, L.tickets), 0, sizeof(int) * 4, s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<unsigned>(work, L.bar), 0, sizeof(unsigned) * 4, s));
     // row permutation from the pivots: compose all n swaps, apply to identity
     int *perm = at<int>(work, L.perm);
     MP_CUDA_TRY(launch_iota(perm, n, s));
@@ -790,16 +789,15 @@ extern "C" int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const in
         MP_CUDA_TRY(launch_apply_moves_vec(perm, at<int2>(work, L.pairs), at<int>(work, L.npairs),
                                            2 * (k2 - k), s));
     }
-    MP_CUDA_TRY(launch_diag_inverses<float>(n, dW, ldw, at<float>(work, L.Linv), at<float>(work, L.Uinv), s));
+    MP_CUDA_TRY(launch_build_inverses<float>(n, dW, ldw, at<float>(work, L.Linv), at<float>(work, L.Uinv),
+                                             at<float>(work, L.invtmp), s));
     MP_CUDA_TRY(launch_col_absmax(n, nrhs, dR, ldr, sb->rnorm, &sb->st, s));
     MP_CUDA_TRY(launch_trsv_lower<float>(n, nrhs, dW, ldw, at<float>(work, L.Linv), dR, ldr, perm, sb->rnorm,
-                                         at<float>(work, L.Y), n, at<float>(work, L.slots),
-                                         at<int>(work, L.flagsL), at<int>(work, L.countsL),
-                                         at<int>(work, L.tickets), 1, &sb->st, s));
+                                         at<float>(work, L.Y), n, at<float>(work, L.acc),
+                                         at<unsigned>(work, L.bar), &sb->st, s));
     MP_CUDA_TRY(launch_trsv_upper<float>(n, nrhs, dW, ldw, at<float>(work, L.Uinv), at<float>(work, L.Y), n,
-                                         at<float>(work, L.Z), n, at<float>(work, L.slots),
-                                         at<int>(work, L.flagsU), at<int>(work, L.countsU),
-                                         at<int>(work, L.tickets) + 1, 1, &sb->st, s));
+                                         at<float>(work, L.Z), n, at<float>(work, L.acc),
+                                         at<unsigned>(work, L.bar), &sb->st, s));
     MP_CUDA_TRY(launch_update<float>(n, nrhs, at<float>(work, L.Z), n, sb->rnorm, dZ, ldz, sb->znorm, 1, s));
     StatusBlock h;
     MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -849,8 +847,8 @@ extern "C" size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec) {
 extern "C" int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl, const float *dU,
                                    int ldu, float *dC, int ldc, void *work, size_t work_bytes, void *stream) {
     g_err[0] = 0;
-    if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP16)
-        return mp_arg_fail(1, "prec must be FP32, BF16 or FP16");
+    if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3)
+        return mp_arg_fail(1, "prec must be FP32, FP16X3, BF16 or FP16");
     if (M < 0) return mp_arg_fail(2, "M < 0");
     if (N < 0) return mp_arg_fail(3, "N < 0");
     if (K < 0) return mp_arg_fail(4, "K < 0");

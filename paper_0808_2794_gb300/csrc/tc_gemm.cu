@@ -30,24 +30,34 @@ namespace {
 constexpr int TILE_J = 128;  // MMA M
 constexpr int TILE_I = 256;  // MMA N
 constexpr int BK = 64;       // 16-bit elements per 128-byte swizzled row
-constexpr int STAGES = 4;
 constexpr int A_BYTES = TILE_J * BK * 2;
 constexpr int B_BYTES = TILE_I * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 64 + NUM_EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int MAX_STAGES = 4;
+
+// SPLIT = 1: one operand pair per stage (bf16 or fp16), 4 stages.
+// SPLIT = 2: operands split in hi + lo fp16 parts (A_hi, A_lo, B_hi, B_lo per
+//            stage), three products per k-step, 2 stages.
+template <int SPLIT> struct TcCfg {
+    static constexpr int STAGE_BYTES = SPLIT * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = SPLIT == 1 ? 4 : 2;
+};
 
 struct __align__(8) TcBarriers {
-    uint64_t full[STAGES];
-    uint64_t empty[STAGES];
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint32_t tmem_base;
     int abort_flag;
 };
 
-constexpr size_t kSmemBytes = (size_t)STAGES * STAGE_BYTES + sizeof(TcBarriers) + 1024;
+template <int SPLIT>
+constexpr size_t smem_bytes() {
+    return (size_t)TcCfg<SPLIT>::STAGES * TcCfg<SPLIT>::STAGE_BYTES + sizeof(TcBarriers) + 1024;
+}
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
@@ -146,10 +156,13 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
            ((uint32_t)(TILE_J >> 4) << 24);
 }
 
-template <uint32_t FMT>
+template <uint32_t FMT, int SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 float *__restrict__ C, long ldc, int M, int N, int KB, MpDevStatus *st) {
+                 float *__restrict__ C, long ldc, int M, int N, int KB, int a_lo_row, int b_lo_row,
+                 const float *__restrict__ inv_scale_p, MpDevStatus *st) {
+    constexpr int STAGES = TcCfg<SPLIT>::STAGES;
+    constexpr int STAGE_BYTES = TcCfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     TcBarriers *bar = reinterpret_cast<TcBarriers *>(smem + (size_t)STAGES * STAGE_BYTES);
@@ -194,8 +207,12 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE_BYTES);
                     const uint32_t fb = smem_u32(&bar->full[stage]);
                     mbar_expect_tx(fb, STAGE_BYTES);
+                    // stage layout: A_hi [A_lo] B_hi [B_lo]
                     tma_load_2d(sa, &mapA, kb * BK, jb * TILE_J, fb);
-                    tma_load_2d(sa + A_BYTES, &mapB, kb * BK, ib * TILE_I, fb);
+                    if (SPLIT == 2) tma_load_2d(sa + A_BYTES, &mapA, kb * BK, a_lo_row + jb * TILE_J, fb);
+                    tma_load_2d(sa + SPLIT * A_BYTES, &mapB, kb * BK, ib * TILE_I, fb);
+                    if (SPLIT == 2)
+                        tma_load_2d(sa + SPLIT * A_BYTES + B_BYTES, &mapB, kb * BK, b_lo_row + ib * TILE_I, fb);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -214,11 +231,16 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     if (!mbar_wait(smem_u32(&bar->full[stage]), phase, abort_flag)) { timed_out = true; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE_BYTES);
-                    const uint32_t sb = sa + A_BYTES;
+                    const uint32_t sb = sa + SPLIT * A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
+                    for (int kk = 0; kk < BK / 16; ++kk) {
                         umma_f16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
                                  (kb | kk) ? 1u : 0u);
+                        if (SPLIT == 2) {  // hi*lo and lo*hi
+                            umma_f16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + B_BYTES + kk * 32), idesc, 1u);
+                            umma_f16(d_tmem, sw128_desc(sa + A_BYTES + kk * 32), sw128_desc(sb + kk * 32), idesc, 1u);
+                        }
+                    }
                     umma_commit(smem_u32(&bar->empty[stage]));
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -231,6 +253,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     } else {  // ------------------------------ epilogue warps 2..9
         const int quarter = warp & 3;        // TMEM lanes this warp may access
         const int half = (warp - 2) >> 2;    // which 128 of the 256 accumulator columns
+        const float inv_scale = SPLIT == 2 ? *inv_scale_p : 1.0f;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -251,7 +274,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * TILE_I + tcol, v);
 #pragma unroll
                 for (int r = 0; r < 32; ++r)
-                    if (cval && row0 + r < M) C[(long)(row0 + r) * ldc + col] = cv[r] - v[r];
+                    if (cval && row0 + r < M) C[(long)(row0 + r) * ldc + col] = fmaf(-inv_scale, v[r], cv[r]);
             }
             tc_fence_before();
             __syncwarp();
@@ -278,12 +301,16 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(floa
 template <> __device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
 
 // Ap[j][k] = fl_p(U[k][j]) for j < N, k < Kpad (zero for k >= K): 32x32 transpose.
-template <typename H>
+// SPLIT == 2: Ap[j] = fp16(s*u) (hi) and Ap[lo_row + j] = fp16(s*u - hi) (lo),
+// s = *scale (a power of two).
+template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
-pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long ldu, H *__restrict__ Ap) {
+pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long ldu, H *__restrict__ Ap, long lo_row,
+                      const float *__restrict__ scale) {
     __shared__ float t[32][33];
     const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const float sc = SPLIT == 2 ? *scale : 1.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int k = k0 + ty + 8 * q, j = j0 + tx;
@@ -293,19 +320,58 @@ pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int j = j0 + ty + 8 * q, k = k0 + tx;
-        if (j < N && k < Kpad) Ap[(long)j * Kpad + k] = to_half<H>(t[tx][ty + 8 * q]);
+        if (j < N && k < Kpad) {
+            const float v = t[tx][ty + 8 * q] * sc;
+            const H hi = to_half<H>(v);
+            Ap[(long)j * Kpad + k] = hi;
+            if constexpr (SPLIT == 2) Ap[(lo_row + j) * Kpad + k] = to_half<H>(v - __half2float(hi));
+        }
     }
 }
 
-// Bp[i][k] = fl_p(L[i][k]) for i < M, k < Kpad (zero for k >= K).
-template <typename H>
+// Bp[i][k] = fl_p(L[i][k]) for i < M, k < Kpad (zero for k >= K); SPLIT as above.
+template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
-pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, H *__restrict__ Bp) {
+pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, H *__restrict__ Bp, long lo_row,
+                 const float *__restrict__ scale) {
     const long total = (long)M * Kpad;
+    const float sc = SPLIT == 2 ? *scale : 1.0f;
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         const int i = (int)(idx / Kpad), k = (int)(idx - (long)i * Kpad);
-        Bp[idx] = to_half<H>(k < K ? L[(long)i * ldl + k] : 0.f);
+        const float v = (k < K ? L[(long)i * ldl + k] : 0.f) * sc;
+        const H hi = to_half<H>(v);
+        Bp[idx] = hi;
+        if constexpr (SPLIT == 2) Bp[lo_row * Kpad + idx] = to_half<H>(v - __half2float(hi));
     }
+}
+
+// max |x| over a rows x cols row-major block -> *out (as uint bits of a non-negative float)
+__global__ void __launch_bounds__(256)
+absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigned *out) {
+    float m = 0.f;
+    const long total = (long)rows * cols;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / cols), c = (int)(idx - (long)r * cols);
+        const float v = fabsf(X[(long)r * ldx + c]);
+        m = (v > m || v != v) ? ((v != v) ? INFINITY : v) : m;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Power-of-two scales: sL = 2^13 (|l| <= 1), sU = 2^(14 - ceil(log2 max|U|));
+// writes sL, sU and 1 / (sL sU).
+__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales) {
+    const float umax = __uint_as_float(*umax_bits);
+    int e = 0;
+    if (umax > 0.f && umax < INFINITY) frexpf(umax, &e);  // umax < 2^e
+    const int eu = 14 - e;
+    const float sL = 8192.0f;
+    const float sU = ldexpf(1.0f, eu);
+    scales[0] = sL;
+    scales[1] = sU;
+    scales[2] = ldexpf(1.0f, -13 - eu);
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -326,7 +392,7 @@ EncodeTiledFn get_encode() {
 }
 
 // 2-D map over a (rows x kpad) K-major 16-bit array, box (64 x box_rows), 128B swizzle.
-cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int kpad, int box_rows, bool bf16) {
+cudaError_t make_map(CUtensorMap *m, const void *base, long rows, int kpad, int box_rows, bool bf16) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
@@ -351,58 +417,95 @@ int num_sms() {
     return sms;
 }
 
-template <typename H, uint32_t FMT>
-cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22,
-                long lda, void *ws, MpDevStatus *st, cudaStream_t s) {
+struct TcWs {
+    void *Ap, *Bp;
+    unsigned *umax;
+    float *scales;
+};
+
+// Scratch layout: [Ap: rowsA x Kpad][Bp: rowsB x Kpad][umax, scales]
+TcWs carve_ws(void *ws, int M, int N, int Kpad, int split) {
+    const long rowsA = split == 2 ? 2L * ((N + TILE_J - 1) / TILE_J * TILE_J) : N;
+    const long rowsB = split == 2 ? 2L * ((M + TILE_I - 1) / TILE_I * TILE_I) : M;
+    char *p = static_cast<char *>(ws);
+    TcWs w;
+    w.Ap = p;
+    p += align_up((size_t)rowsA * Kpad * 2, 1024);
+    w.Bp = p;
+    p += align_up((size_t)rowsB * Kpad * 2, 1024);
+    w.umax = reinterpret_cast<unsigned *>(p);
+    w.scales = reinterpret_cast<float *>(p + 16);
+    return w;
+}
+
+template <typename H, uint32_t FMT, int SPLIT>
+cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22, long lda,
+                void *ws, MpDevStatus *st, cudaStream_t s) {
     const int Kpad = (K + BK - 1) / BK * BK;
-    H *Ap = reinterpret_cast<H *>(ws);
-    H *Bp = reinterpret_cast<H *>(static_cast<char *>(ws) + align_up((size_t)N * Kpad * sizeof(H), 1024));
+    TcWs w = carve_ws(ws, M, N, Kpad, SPLIT);
+    H *Ap = reinterpret_cast<H *>(w.Ap);
+    H *Bp = reinterpret_cast<H *>(w.Bp);
+    const long a_lo = SPLIT == 2 ? (long)(N + TILE_J - 1) / TILE_J * TILE_J : 0;
+    const long b_lo = SPLIT == 2 ? (long)(M + TILE_I - 1) / TILE_I * TILE_I : 0;
+    cudaError_t e;
+    if (SPLIT == 2) {
+        // padding rows of the hi halves must be zero
+        e = cudaMemsetAsync(Ap, 0, (size_t)2 * a_lo * Kpad * sizeof(H), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(Bp, 0, (size_t)2 * b_lo * Kpad * sizeof(H), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(w.umax, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        const long tot = (long)K * N;
+        mp_note_launch();
+        absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(K, N, U12, ldu, w.umax);
+        mp_note_launch();
+        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales);
+    }
     {
         dim3 grid((N + 31) / 32, (Kpad + 31) / 32);
         mp_note_launch();
-        pack_transpose_kernel<H><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap);
+        pack_transpose_kernel<H, SPLIT><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
         const long total = (long)M * Kpad;
         const int blocks = (int)std::min<long>((total + 255) / 256, 4L * 1024);
         mp_note_launch();
-        pack_rows_kernel<H><<<blocks, 256, 0, s>>>(M, K, Kpad, L21, ldl, Bp);
-        cudaError_t e = cudaGetLastError();
+        pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(M, K, Kpad, L21, ldl, Bp, b_lo, w.scales);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     CUtensorMap mapA, mapB;
-    cudaError_t e = make_map(&mapA, Ap, N, Kpad, TILE_J, FMT == 1);
+    e = make_map(&mapA, Ap, SPLIT == 2 ? 2 * a_lo : N, Kpad, TILE_J, FMT == 1);
     if (e != cudaSuccess) return e;
-    e = make_map(&mapB, Bp, M, Kpad, TILE_I, FMT == 1);
+    e = make_map(&mapB, Bp, SPLIT == 2 ? 2 * b_lo : M, Kpad, TILE_I, FMT == 1);
     if (e != cudaSuccess) return e;
-    auto kern = tc_update_kernel<FMT>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    auto kern = tc_update_kernel<FMT, SPLIT>;
+    constexpr size_t smem = smem_bytes<SPLIT>();
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int ntiles = ((M + TILE_I - 1) / TILE_I) * ((N + TILE_J - 1) / TILE_J);
     const int grid = std::min(ntiles, num_sms());
     mp_note_launch();
-    kern<<<grid, NUM_THREADS, kSmemBytes, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BK, st);
+    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BK, (int)a_lo, (int)b_lo,
+                                         w.scales + 2, st);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t tc_workspace_bytes(int n, int nb, int prec) {
-    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP16) return 0;
+    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3) return 0;
     const size_t kpad = (size_t)(nb + BK - 1) / BK * BK;
-    return align_up((size_t)n * kpad * 2, 1024) * 2 + 1024;
+    const int split = prec == MP_PREC_FP16X3 ? 2 : 1;
+    const size_t rowsA = split == 2 ? 2 * ((size_t)(n + TILE_J - 1) / TILE_J * TILE_J) : (size_t)n;
+    const size_t rowsB = split == 2 ? 2 * ((size_t)(n + TILE_I - 1) / TILE_I * TILE_I) : (size_t)n;
+    return align_up(rowsA * kpad * 2, 1024) + align_up(rowsB * kpad * 2, 1024) + 1024;
 }
 
 cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, long ldl, const float *U12,
                                long ldu, float *A22, long lda, void *ws, MpDevStatus *st, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
-    if (prec == MP_PREC_FP16) return run<__half, 0>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     return cudaErrorInvalidValue;
-}
-
-cudaError_t tc_gemm_sub(int prec, int M, int N, int K, const float *A, long lda, const float *B, long ldb,
-                        float *C, long ldc, void *ws, size_t ws_bytes, MpDevStatus *st, cudaStream_t s) {
-    const int Kpad = (K + BK - 1) / BK * BK;
-    const size_t need = align_up((size_t)N * Kpad * 2, 1024) + align_up((size_t)M * Kpad * 2, 1024);
-    if (ws_bytes < need) return cudaErrorInvalidValue;
-    return tc_trailing_update(prec, M, N, K, A, lda, B, ldb, C, ldc, ws, st, s);
 }

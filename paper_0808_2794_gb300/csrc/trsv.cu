@@ -2,19 +2,20 @@
 // L y = P r and U z = y (Algorithm 1 steps 2-3 and 5-6; SGETRS, Section
 // 3.1.1).
 //
-// GB300 design.  The factors are row-major, so every block row of L (or U)
-// is a set of contiguous row segments.  The n rows are cut into BS-row
-// blocks (BS = 128 for FP32, 64 for FP64); the diagonal blocks are inverted
-// once after the factorization, so that a block's own solve is a small
-// parallel matrix-vector product.  The off-diagonal work of block row i is
-// split into chunks of kChunk blocks; every (block row, chunk) pair is one
-// CTA that streams its part of the row as soon as the blocks it needs are
-// published (per-block flags), writes a partial sum to its own slot, and
-// counts itself in.  The CTA that completes the last chunk of a row adds the
-// slots in a fixed order (deterministic), applies the inverted diagonal
-// block and publishes the block.  CTAs take work items from an atomic ticket
-// in dependency order, so a CTA only waits on items that already run; every
-// wait is bounded and reports MP_FLAG_TIMEOUT if it gives up.
+// GB300 design.  The factors are row-major.  Once per factorization the
+// diagonal blocks of L and U are inverted at a large block size BI (1024
+// rows in FP32 for n >= 2048): 128-row (64 in FP64) blocks are inverted by
+// substitution, then neighbours are merged level by level with batched
+// GEMMs (X21 = -X22 L21 X11 for L, X12 = -X11 U12 X22 for U).  A solve is
+// then only n/BI dependent steps of one persistent cooperative kernel:
+//   A. y_b = inv(D_b) acc_b           (a BI x BI matrix-vector product)
+//   -- grid barrier --
+//   B. acc_r -= W[r, block b] y_b for every row r still to be solved
+//      (streams the block column of the factor once, coalesced rows)
+//   -- grid barrier --
+// so the dependency chain is n/BI long instead of n, and every step streams
+// its part of the factor with all SMs.  Grid barriers are bounded and report
+// MP_FLAG_TIMEOUT instead of hanging.
 //
 // The right-hand side r (FP64) is scaled by s = 2^ceil(log2 ||r||inf) before
 // it is rounded to the working precision (exact power-of-two scaling keeps
@@ -25,7 +26,7 @@
 namespace {
 
 constexpr int kMaxRhs = 8;
-constexpr int kChunk = 8;  // dependency blocks per CTA
+constexpr int kThreads = 256;
 
 __device__ __forceinline__ double pow2_ceil(double v) {
     if (!(v > 0.0) || !(v <= 1.79769313486231570815e308)) return 1.0;
@@ -34,16 +35,20 @@ __device__ __forceinline__ double pow2_ceil(double v) {
     return (m == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
 }
 
-// ---- inverses of the diagonal blocks ---------------------------------------
+template <typename T> constexpr int base_bs() { return sizeof(T) == 4 ? 128 : 64; }
+
+// ---- inverses of the base diagonal blocks, written into the BI x BI layout
 template <typename T, int BS>
 __global__ void __launch_bounds__(BS)
-diag_inverse_kernel(int n, const T *__restrict__ W, long ldw, T *__restrict__ Linv, T *__restrict__ Uinv) {
+base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restrict__ Linv, T *__restrict__ Uinv) {
     extern __shared__ __align__(16) unsigned char raw[];
     T(*blk)[BS + 1] = reinterpret_cast<T(*)[BS + 1]>(raw);
     T(*x)[BS + 1] = reinterpret_cast<T(*)[BS + 1]>(raw + sizeof(T) * BS * (BS + 1));
-    const int b = blockIdx.x, c = threadIdx.x;
-    const int r0 = b * BS;
+    const int g = blockIdx.x, c = threadIdx.x;
+    const int r0 = g * BS;
     const int bs = min(BS, n - r0);
+    const int big = r0 / BI, o = r0 - big * BI;
+    const long dst = (long)big * BI * BI + (long)o * BI + o;  // top-left of the sub-block
     for (int i = 0; i < BS; ++i) {
         const bool in = (i < bs) && (c < bs);
         blk[i][c] = in ? W[(long)(r0 + i) * ldw + r0 + c] : T(i == c ? 1 : 0);
@@ -55,240 +60,341 @@ diag_inverse_kernel(int n, const T *__restrict__ W, long ldw, T *__restrict__ Li
         for (int l = c; l < i; ++l) s = fma(-blk[i][l], x[l][c], s);
         x[i][c] = (i < c) ? T(0) : s;
     }
-    T *Lo = Linv + (long)b * BS * BS;
-    for (int i = 0; i < BS; ++i) Lo[i * BS + c] = x[i][c];
+    for (int i = 0; i < bs; ++i)
+        if (c < bs) Linv[dst + (long)i * BI + c] = x[i][c];
     // upper: x_i = (delta_ic - sum_{l>i} U_il x_l) / U_ii
     for (int i = BS - 1; i >= 0; --i) {
         T s = T(i == c ? 1 : 0);
         for (int l = i + 1; l <= c; ++l) s = fma(-blk[i][l], x[l][c], s);
         x[i][c] = (i > c) ? T(0) : s / blk[i][i];
     }
-    T *Uo = Uinv + (long)b * BS * BS;
-    for (int i = 0; i < BS; ++i) Uo[i * BS + c] = x[i][c];
+    for (int i = 0; i < bs; ++i)
+        if (c < bs) Uinv[dst + (long)i * BI + c] = x[i][c];
 }
 
-__host__ __device__ __forceinline__ int nchunks(int deps) { return (deps + kChunk - 1) / kChunk; }
-
-// Work items of the block rows before solve position q (the row at position
-// q has q dependencies): sum over q' < q of max(1, nchunks(q')).
-__host__ __device__ __forceinline__ long items_before(int q) {
-    if (q <= 0) return 0;
-    const long C = kChunk;
-    const long Q = q - 1;  // positions 1..Q contribute ceil(q'/C) each, position 0 one item
-    const long full = Q / C, rem = Q % C;
-    return 1 + C * full * (full + 1) / 2 + (full + 1) * rem;
+// ---- grid-wide barrier for a cooperative launch (bounded wait)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, MpDevStatus *st,
+                                             bool *abort_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned *)gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            long long polls = 0;
+            while (*gen == g) {
+                if (++polls > (1LL << 24) || global_ns() - t0 > 1000000000ULL) {
+                    mp_flag(st, MP_FLAG_TIMEOUT);
+                    atomicExch(&st->timeout_site, 2);
+                    *abort_s = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !*abort_s;
 }
 
-// One CTA per (block row, chunk).  Thread (r = tid / TPR, part = tid % TPR)
-// owns row r of the block and a BS/TPR-column segment of each block.
-template <typename T, int BS, bool LOWER>
-__global__ void __launch_bounds__(256)
-trsv_chunk_kernel(int n, int nrhs, const T *__restrict__ W, long ldw, const T *__restrict__ Dinv,
-                  const double *__restrict__ R, long ldr, const int *__restrict__ perm,
-                  const double *__restrict__ rnorm, const T *__restrict__ Yin, long ldyin,
-                  T *__restrict__ Yout, long ldyout, T *__restrict__ slots, int *flags, int *counts,
-                  int *ticket, int epoch, long items_per_solve, MpDevStatus *st) {
-    constexpr int TPR = 256 / BS;  // threads per row (2 for BS=128, 4 for BS=64)
-    constexpr int SEG = BS / TPR;  // columns per thread per block
-    __shared__ int s_q, s_c, s_ready;
-    __shared__ bool s_ok, s_last;
-    __shared__ T ys[kMaxRhs][BS];  // y of the current dependency block
-    __shared__ T accs[kMaxRhs][BS];
-    const int tid = threadIdx.x;
-    const int r = tid / TPR, part = tid % TPR;
-    const int nblk = (n + BS - 1) / BS;
-    if (tid == 0) {
-        const long t = (long)atomicAdd(ticket, 1) - (long)(epoch - 1) * items_per_solve;
-        int lo = 0, hi = nblk - 1;  // largest q with items_before(q) <= t
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (items_before(mid) <= t) lo = mid; else hi = mid - 1;
-        }
-        s_q = lo;
-        s_c = (int)(t - items_before(lo));
-        s_ok = true;
-        s_last = false;
-    }
-    __syncthreads();
-    const int q = s_q, c = s_c;
-    const int i = LOWER ? q : nblk - 1 - q;  // block row
-    const int row = i * BS + r;
-    const bool rvalid = row < n;
-    const int nch = nchunks(q);
-    T part_acc[kMaxRhs];
-#pragma unroll
-    for (int h = 0; h < kMaxRhs; ++h) part_acc[h] = T(0);
+// Vector type of 16 bytes.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
 
-    if (nch > 0) {
-        // dependencies at solve positions [d0, d1); block column j = position
-        // (lower) or nblk-1-position (upper)
-        const int d0 = c * kChunk, d1 = min(q, d0 + kChunk);
-        int ready = d0;
-        for (int d = d0; d < d1; ++d) {
-            const int j = LOWER ? d : nblk - 1 - d;
-            if (d == ready) {
-                if (tid == 0) {
-                    const volatile int *vf = flags;
-                    bool ok = wait_flag_geq(vf + j, epoch, st, 1);
-                    int e = d + 1;
-                    while (ok && e < d1 && vf[LOWER ? e : nblk - 1 - e] >= epoch) ++e;
-                    __threadfence();
-                    s_ready = e;
-                    if (!ok) s_ok = false;
-                }
-                __syncthreads();
-                if (!s_ok) break;
-                ready = s_ready;
-            }
-            for (int idx = tid; idx < nrhs * BS; idx += 256) {  // stage y_j
-                const int h = idx / BS, k = idx % BS;
-                const int col = j * BS + k;
-                ys[h][k] = col < n ? __ldcg(Yout + (long)h * ldyout + col) : T(0);
-            }
-            __syncthreads();
-            if (rvalid) {
-                const int c0 = j * BS + part * SEG;
-                const T *wrow = W + (long)row * ldw + c0;
-                T wv[SEG];
+// Dot products of one row segment (bs <= 1024 elements for FP32, <= 512 for
+// FP64, 16-byte aligned) with nrhs vectors staged in shared memory (stride BI,
+// zero beyond bs).  Each lane issues all its 16-byte loads before any FMA, so a
+// row costs one memory latency.  Returns the warp-reduced sums in every lane.
+template <typename T, bool STREAM>
+__device__ __forceinline__ void row_dot(const T *__restrict__ src, int bs, const T *vs, int BI, int nrhs,
+                                        T (&sum)[kMaxRhs]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int STRIDE = 32 * VW;
+    constexpr int NQ = (sizeof(T) == 4 ? 1024 : 512) / STRIDE;
+    const int lane = threadIdx.x & 31;
+    T w[NQ][VW];
 #pragma unroll
-                for (int qq = 0; qq < SEG; ++qq) wv[qq] = (c0 + qq < n) ? wrow[qq] : T(0);
+    for (int q = 0; q < NQ; ++q) {
+        const int k = q * STRIDE + lane * VW;
+        if (k + VW <= bs) {
+            const V v = STREAM ? __ldcs(reinterpret_cast<const V *>(src + k)) : *reinterpret_cast<const V *>(src + k);
+            const T *e = reinterpret_cast<const T *>(&v);
 #pragma unroll
-                for (int h = 0; h < kMaxRhs; ++h) {
-                    if (h < nrhs) {
-                        T acc = part_acc[h];
+            for (int t = 0; t < VW; ++t) w[q][t] = e[t];
+        } else {
 #pragma unroll
-                        for (int qq = 0; qq < SEG; ++qq) acc = fma(wv[qq], ys[h][part * SEG + qq], acc);
-                        part_acc[h] = acc;
-                    }
-                }
-            }
-            __syncthreads();  // ys is reused by the next block
-        }
-        if (!s_ok) return;  // timeout recorded in the status block
-#pragma unroll
-        for (int h = 0; h < kMaxRhs; ++h)
-#pragma unroll
-            for (int off = 1; off < TPR; off <<= 1) part_acc[h] += __shfl_xor_sync(0xffffffffu, part_acc[h], off);
-        if (part == 0) {
-            T *slot = slots + (items_before(q) + c) * kMaxRhs * BS;
-            for (int h = 0; h < nrhs; ++h) slot[h * BS + r] = part_acc[h];
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const int old = atomicAdd(&counts[i], 1);
-            s_last = (old + 1 == epoch * nch);
-        }
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-    }
-    // ---- the last chunk of block row i: acc = rhs - sum of the chunk partials
-    if (part == 0) {
-#pragma unroll 1
-        for (int h = 0; h < nrhs; ++h) {
-            T sum = T(0);
-            for (int cc = 0; cc < nch; ++cc)
-                sum += __ldcg(slots + ((items_before(q) + cc) * kMaxRhs + h) * BS + r);
-            T rhs = T(0);
-            if (rvalid) {
-                if (LOWER) {
-                    const double s = pow2_ceil(rnorm[h]);
-                    rhs = (T)(R[(long)h * ldr + perm[row]] / s);
-                } else {
-                    rhs = Yin[(long)h * ldyin + row];
-                }
-            }
-            accs[h][r] = rvalid ? rhs - sum : T(0);
+            for (int t = 0; t < VW; ++t) w[q][t] = (k + t < bs) ? src[k + t] : T(0);
         }
     }
-    __syncthreads();
-    // y_i = Dinv_i * acc
-    const T *D = Dinv + (long)i * BS * BS + (long)r * BS + part * SEG;
-    T dv[SEG];
 #pragma unroll
-    for (int qq = 0; qq < SEG; ++qq) dv[qq] = D[qq];
-    for (int h = 0; h < nrhs; ++h) {
+    for (int h = 0; h < kMaxRhs; ++h) {
         T acc = T(0);
+        if (h < nrhs) {
 #pragma unroll
-        for (int qq = 0; qq < SEG; ++qq) acc = fma(dv[qq], accs[h][part * SEG + qq], acc);
+            for (int q = 0; q < NQ; ++q) {
+                const int k = q * STRIDE + lane * VW;
+                if (k < bs) {
+                    const V y = *reinterpret_cast<const V *>(vs + h * BI + k);
+                    const T *ye = reinterpret_cast<const T *>(&y);
 #pragma unroll
-        for (int off = 1; off < TPR; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (part == 0 && rvalid) Yout[(long)h * ldyout + row] = acc;
+                    for (int t = 0; t < VW; ++t) acc = fma(w[q][t], ye[t], acc);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        }
+        sum[h] = acc;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) atomicExch(&flags[i], epoch);
+}
+
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(kThreads)
+trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ldw, const T *__restrict__ Inv,
+                       const double *__restrict__ R, long ldr, const int *__restrict__ perm,
+                       const double *__restrict__ rnorm, const T *__restrict__ Yin, long ldyin,
+                       T *__restrict__ Yout, long ldyout, T *__restrict__ acc, unsigned *bar_count,
+                       unsigned *bar_gen, MpDevStatus *st) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    T *vs = reinterpret_cast<T *>(raw);  // nrhs x BI vector of the current block
+    __shared__ bool abort_s;
+    if (threadIdx.x == 0) abort_s = false;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (kThreads / 32);
+    const long gtid = (long)blockIdx.x * kThreads + threadIdx.x;
+    const long gthreads = (long)gridDim.x * kThreads;
+    const int nbi = (n + BI - 1) / BI;
+
+    // acc = right-hand side (P r / s for L; y for U)
+    for (long idx = gtid; idx < (long)nrhs * n; idx += gthreads) {
+        const int h = (int)(idx / n), r = (int)(idx - (long)h * n);
+        T v;
+        if (LOWER) {
+            const double s = pow2_ceil(rnorm[h]);
+            v = (T)(R[(long)h * ldr + perm[r]] / s);
+        } else {
+            v = Yin[(long)h * ldyin + r];
+        }
+        acc[(long)h * n + r] = v;
+    }
+    if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
+
+    for (int step = 0; step < nbi; ++step) {
+        const int b = LOWER ? step : nbi - 1 - step;
+        const int r0 = b * BI;
+        const int bs = min(BI, n - r0);
+        // ---- A: y_b = inv(D_b) acc_b
+        for (int idx = threadIdx.x; idx < nrhs * BI; idx += kThreads) {
+            const int h = idx / BI, k = idx - h * BI;
+            vs[idx] = k < bs ? __ldcg(acc + (long)h * n + r0 + k) : T(0);
+        }
+        __syncthreads();
+        const T *D = Inv + (long)b * BI * BI;
+        for (int r = gwarp; r < bs; r += nwarps) {
+            T sum[kMaxRhs];
+            row_dot<T, false>(D + (long)r * BI, bs, vs, BI, nrhs, sum);
+            if (lane == 0)
+#pragma unroll
+                for (int h = 0; h < kMaxRhs; ++h)
+                    if (h < nrhs) Yout[(long)h * ldyout + r0 + r] = sum[h];
+        }
+        if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
+        // ---- B: acc_r -= W[r, block b] y_b for the rows still to be solved
+        const int lo = LOWER ? r0 + bs : 0;
+        const int hi = LOWER ? n : r0;
+        if (lo >= hi) continue;  // last step: nothing left to update
+        for (int idx = threadIdx.x; idx < nrhs * BI; idx += kThreads) {
+            const int h = idx / BI, k = idx - h * BI;
+            vs[idx] = k < bs ? __ldcg(Yout + (long)h * ldyout + r0 + k) : T(0);
+        }
+        __syncthreads();
+        for (int r = lo + gwarp; r < hi; r += nwarps) {
+            T sum[kMaxRhs];
+            row_dot<T, true>(W + (long)r * ldw + r0, bs, vs, BI, nrhs, sum);
+            if (lane == 0)
+#pragma unroll
+                for (int h = 0; h < kMaxRhs; ++h)
+                    if (h < nrhs) acc[(long)h * n + r] -= sum[h];
+        }
+        if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
+    }
+}
+
+int num_sms_cached() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+template <typename T, bool LOWER>
+cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, const T *Inv, const double *R, long ldr,
+                              const int *perm, const double *rnorm, const T *Yin, long ldyin, T *Yout, long ldyout,
+                              T *acc, unsigned *bar, MpDevStatus *st, cudaStream_t s) {
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
+    auto kern = trsv_persistent_kernel<T, LOWER>;
+    const size_t smem = sizeof(T) * (size_t)kMaxRhs * BI;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = num_sms_cached() * std::min(per_sm, 2);
+    unsigned *cnt = bar, *gen = bar + 1;
+    void *args[] = {(void *)&n,    (void *)&nrhs,  (void *)&BI,    (void *)&W,    (void *)&ldw,
+                    (void *)&Inv,  (void *)&R,     (void *)&ldr,   (void *)&perm, (void *)&rnorm,
+                    (void *)&Yin,  (void *)&ldyin, (void *)&Yout,  (void *)&ldyout, (void *)&acc,
+                    (void *)&cnt,  (void *)&gen,   (void *)&st};
+    mp_note_launch();
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace
 
 template <typename T>
-int trsv_block_size() { return sizeof(T) == 4 ? 128 : 64; }
-template int trsv_block_size<float>();
-template int trsv_block_size<double>();
-
-size_t trsv_slot_bytes(int n, int bs, size_t elem) {
-    const int nblk = (n + bs - 1) / bs;
-    return (size_t)items_before(nblk) * kMaxRhs * bs * elem;
+int trsv_inverse_block(int n) {
+    const int base = base_bs<T>();
+    const int top = sizeof(T) == 4 ? 1024 : 512;
+    int bi = base;
+    while (bi < top && bi < n) bi *= 2;
+    return bi;
 }
+template int trsv_inverse_block<float>(int);
+template int trsv_inverse_block<double>(int);
 
 template <typename T>
-cudaError_t launch_diag_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, cudaStream_t s) {
-    constexpr int BS = sizeof(T) == 4 ? 128 : 64;
-    const int nblk = (n + BS - 1) / BS;
-    if (nblk == 0) return cudaSuccess;
-    auto kern = diag_inverse_kernel<T, BS>;
-    const size_t smem = 2 * sizeof(T) * BS * (BS + 1);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    mp_note_launch();
-    kern<<<nblk, BS, smem, s>>>(n, W, ldw, Linv, Uinv);
-    return cudaGetLastError();
+size_t trsv_inverse_bytes(int n) {
+    const int BI = trsv_inverse_block<T>(n);
+    const size_t nbi = (size_t)(n + BI - 1) / BI;
+    return nbi * BI * BI * sizeof(T);
 }
-template cudaError_t launch_diag_inverses<float>(int, const float *, long, float *, float *, cudaStream_t);
-template cudaError_t launch_diag_inverses<double>(int, const double *, long, double *, double *, cudaStream_t);
+template size_t trsv_inverse_bytes<float>(int);
+template size_t trsv_inverse_bytes<double>(int);
+
+template <typename T>
+size_t trsv_tmp_bytes(int n) {
+    const int BI = trsv_inverse_block<T>(n);
+    const size_t nbi = (size_t)(n + BI - 1) / BI;
+    return nbi * (size_t)BI * BI / 4 * sizeof(T) + 256;
+}
+template size_t trsv_tmp_bytes<float>(int);
+template size_t trsv_tmp_bytes<double>(int);
+
+// Builds inv(L_bb) and inv(U_bb) for the BI x BI diagonal blocks of the
+// row-major factors in W.  tmp holds trsv_tmp_bytes<T>(n).
+template <typename T>
+cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    constexpr int BS = base_bs<T>();
+    const int BI = trsv_inverse_block<T>(n);
+    const int nbi = (n + BI - 1) / BI;
+    const size_t bytes = (size_t)nbi * BI * BI * sizeof(T);
+    cudaError_t e = cudaMemsetAsync(Linv, 0, bytes, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(Uinv, 0, bytes, s);
+    if (e != cudaSuccess) return e;
+    {
+        auto kern = base_inverse_kernel<T, BS>;
+        const size_t smem = 2 * sizeof(T) * BS * (BS + 1);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        mp_note_launch();
+        kern<<<(n + BS - 1) / BS, BS, smem, s>>>(n, BI, W, ldw, Linv, Uinv);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int nfull = n / BI;
+    const long BB = (long)BI * BI;
+    for (int h = BS; h < BI; h *= 2) {
+        const int pairs = BI / (2 * h);
+        // full BI blocks: batched over (block, pair)
+        if (nfull > 0) {
+            const int batch = nfull * pairs;
+            const long wo = (long)BI * ldw + BI, wi = (long)2 * h * ldw + 2 * h;   // W strides
+            const long io = BB, ii = (long)2 * h * BI + 2 * h;                      // inverse strides
+            const long to = (long)pairs * h * h, ti = (long)h * h;                  // tmp strides
+            // L: T = L21 X11 ; X21 = -X22 T
+            e = launch_gemm_batched<T>(h, h, h, T(1), T(0), W + (long)h * ldw, ldw, Linv, BI, tmp, h, batch, pairs,
+                                       wo, wi, io, ii, to, ti, s);
+            if (e != cudaSuccess) return e;
+            e = launch_gemm_batched<T>(h, h, h, T(-1), T(0), Linv + (long)h * BI + h, BI, tmp, h,
+                                       Linv + (long)h * BI, BI, batch, pairs, io, ii, to, ti, io, ii, s);
+            if (e != cudaSuccess) return e;
+            // U: T = U12 X22 ; X12 = -X11 T
+            e = launch_gemm_batched<T>(h, h, h, T(1), T(0), W + h, ldw, Uinv + (long)h * BI + h, BI, tmp, h, batch,
+                                       pairs, wo, wi, io, ii, to, ti, s);
+            if (e != cudaSuccess) return e;
+            e = launch_gemm_batched<T>(h, h, h, T(-1), T(0), Uinv, BI, tmp, h, Uinv + h, BI, batch, pairs, io, ii,
+                                       to, ti, io, ii, s);
+            if (e != cudaSuccess) return e;
+        }
+        // the partial last block: pair by pair with clipped sizes
+        if (nfull < nbi) {
+            const int base = nfull * BI;
+            T *Lb = Linv + (long)nfull * BB, *Ub = Uinv + (long)nfull * BB;
+            for (int p = 0; p < pairs; ++p) {
+                const int o1 = p * 2 * h, o2 = o1 + h;
+                if (base + o2 >= n) break;
+                const int h2 = std::min(h, n - (base + o2));
+                const T *L21 = W + (long)(base + o2) * ldw + base + o1;
+                const T *U12 = W + (long)(base + o1) * ldw + base + o2;
+                e = launch_gemm_batched<T>(h2, h, h, T(1), T(0), L21, ldw, Lb + (long)o1 * BI + o1, BI, tmp, h, 1, 1,
+                                           0, 0, 0, 0, 0, 0, s);
+                if (e != cudaSuccess) return e;
+                e = launch_gemm_batched<T>(h2, h, h2, T(-1), T(0), Lb + (long)o2 * BI + o2, BI, tmp, h,
+                                           Lb + (long)o2 * BI + o1, BI, 1, 1, 0, 0, 0, 0, 0, 0, s);
+                if (e != cudaSuccess) return e;
+                e = launch_gemm_batched<T>(h, h2, h2, T(1), T(0), U12, ldw, Ub + (long)o2 * BI + o2, BI, tmp, h2, 1, 1,
+                                           0, 0, 0, 0, 0, 0, s);
+                if (e != cudaSuccess) return e;
+                e = launch_gemm_batched<T>(h, h2, h, T(-1), T(0), Ub + (long)o1 * BI + o1, BI, tmp, h2,
+                                           Ub + (long)o1 * BI + o2, BI, 1, 1, 0, 0, 0, 0, 0, 0, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+template cudaError_t launch_build_inverses<float>(int, const float *, long, float *, float *, float *, cudaStream_t);
+template cudaError_t launch_build_inverses<double>(int, const double *, long, double *, double *, double *,
+                                                   cudaStream_t);
 
 template <typename T>
 cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv, const double *R, long ldr,
-                              const int *perm, const double *rnorm, T *Y, long ldy, T *slots, int *flags,
-                              int *counts, int *ticket, int epoch, MpDevStatus *st, cudaStream_t s) {
-    constexpr int BS = sizeof(T) == 4 ? 128 : 64;
-    if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
-    const int nblk = (n + BS - 1) / BS;
-    if (nblk == 0) return cudaSuccess;
-    const long items = items_before(nblk);
-    mp_note_launch();
-    trsv_chunk_kernel<T, BS, true><<<(unsigned)items, 256, 0, s>>>(n, nrhs, W, ldw, Linv, R, ldr, perm, rnorm,
-                                                                   nullptr, 0, Y, ldy, slots, flags, counts,
-                                                                   ticket, epoch, items, st);
-    return cudaGetLastError();
+                              const int *perm, const double *rnorm, T *Y, long ldy, T *acc, unsigned *bar,
+                              MpDevStatus *st, cudaStream_t s) {
+    return launch_persistent<T, true>(n, nrhs, trsv_inverse_block<T>(n), W, ldw, Linv, R, ldr, perm, rnorm,
+                                      nullptr, 0, Y, ldy, acc, bar, st, s);
 }
 template cudaError_t launch_trsv_lower<float>(int, int, const float *, long, const float *, const double *, long,
-                                              const int *, const double *, float *, long, float *, int *, int *,
-                                              int *, int, MpDevStatus *, cudaStream_t);
+                                              const int *, const double *, float *, long, float *, unsigned *,
+                                              MpDevStatus *, cudaStream_t);
 template cudaError_t launch_trsv_lower<double>(int, int, const double *, long, const double *, const double *,
-                                               long, const int *, const double *, double *, long, double *, int *,
-                                               int *, int *, int, MpDevStatus *, cudaStream_t);
+                                               long, const int *, const double *, double *, long, double *,
+                                               unsigned *, MpDevStatus *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_trsv_upper(int n, int nrhs, const T *W, long ldw, const T *Uinv, const T *Y, long ldy, T *Z,
-                              long ldz, T *slots, int *flags, int *counts, int *ticket, int epoch,
-                              MpDevStatus *st, cudaStream_t s) {
-    constexpr int BS = sizeof(T) == 4 ? 128 : 64;
-    if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
-    const int nblk = (n + BS - 1) / BS;
-    if (nblk == 0) return cudaSuccess;
-    const long items = items_before(nblk);
-    mp_note_launch();
-    trsv_chunk_kernel<T, BS, false><<<(unsigned)items, 256, 0, s>>>(n, nrhs, W, ldw, Uinv, nullptr, 0, nullptr,
-                                                                    nullptr, Y, ldy, Z, ldz, slots, flags, counts,
-                                                                    ticket, epoch, items, st);
-    return cudaGetLastError();
+                              long ldz, T *acc, unsigned *bar, MpDevStatus *st, cudaStream_t s) {
+    return launch_persistent<T, false>(n, nrhs, trsv_inverse_block<T>(n), W, ldw, Uinv, nullptr, 0, nullptr,
+                                       nullptr, Y, ldy, Z, ldz, acc, bar, st, s);
 }
 template cudaError_t launch_trsv_upper<float>(int, int, const float *, long, const float *, const float *, long,
-                                              float *, long, float *, int *, int *, int *, int, MpDevStatus *,
-                                              cudaStream_t);
+                                              float *, long, float *, unsigned *, MpDevStatus *, cudaStream_t);
 template cudaError_t launch_trsv_upper<double>(int, int, const double *, long, const double *, const double *,
-                                               long, double *, long, double *, int *, int *, int *, int,
-                                               MpDevStatus *, cudaStream_t);
+                                               long, double *, long, double *, unsigned *, MpDevStatus *,
+                                               cudaStream_t);

@@ -63,9 +63,10 @@ def test_workspace_queries_scale(lib):
     o = solver.default_opts()
     w1 = lib.mp_gesv_workspace_bytes(1024, 1, ctypes.byref(o))
     w2 = lib.mp_gesv_workspace_bytes(2048, 1, ctypes.byref(o))
-    # dominated by the n^2 working matrix (FP64 room for the fallback)
-    assert 8 * 1024 * 1024 <= w1 < 16 * 1024 * 1024
-    assert 3.5 < w2 / w1 < 4.5
+    # dominated by the n^2 working matrix (FP64 room for the fallback) and the
+    # inverted diagonal blocks of the factors (n x BI per triangle)
+    assert 8 * 1024 * 1024 <= w1 < 32 * 1024 * 1024
+    assert 2.5 < w2 / w1 < 4.5
     o.allow_fallback = 0
-    assert lib.mp_gesv_workspace_bytes(2048, 1, ctypes.byref(o)) < w2 * 0.6
+    assert lib.mp_gesv_workspace_bytes(2048, 1, ctypes.byref(o)) < w2 * 0.75
     assert lib.mp_factor_ld(1) == 32 and lib.mp_factor_ld(33) == 64
