@@ -24,6 +24,7 @@
 // the composed row permutation as (destination, source) moves for the row
 // exchange of the rest of the matrix.
 #include <climits>
+#include <cstddef>
 #include <type_traits>
 
 #include "common.cuh"
@@ -72,30 +73,84 @@ template <> struct Cand<double> {
     }
 };
 
-template <typename T>
-__device__ __forceinline__ Cand<T> warp_best(Cand<T> c) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const Cand<T> o = c.shfl_xor(off);
-        if (o.better(c)) c = o;
-    }
-    return c;
+// Warp-wide best candidate with redux.sync (maximum of the key words, most
+// significant first); every lane receives it.
+__device__ __forceinline__ Cand<float> warp_best(Cand<float> c) {
+    const unsigned hi = (unsigned)(c.k >> 32), lo = (unsigned)c.k;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    return Cand<float>{((unsigned long long)mhi << 32) | mlo};
 }
+__device__ __forceinline__ Cand<double> warp_best(Cand<double> c) {
+    // magnitude bits (non-negative doubles order like unsigned integers; "none"
+    // maps to zero), then the smallest row among equal magnitudes
+    const unsigned long long b = c.i == INT_MAX ? 0ull : (unsigned long long)__double_as_longlong(c.v);
+    const unsigned inv = c.i == INT_MAX ? 0u : 0xFFFFFFFFu - (unsigned)c.i;
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const unsigned minv = __reduce_max_sync(0xffffffffu, (hi == mhi && lo == mlo) ? inv : 0u);
+    if (minv == 0u) return Cand<double>::none();
+    return Cand<double>{__longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo)),
+                        (int)(0xFFFFFFFFu - minv)};
+}
+
+// Lane holding the best candidate among the lanes (the first such lane).
+template <typename T>
+__device__ __forceinline__ int best_lane(const Cand<T> &mine, const Cand<T> &best) {
+    const bool eq = !(best.better(mine)) && !(mine.better(best));
+    return __ffs(__ballot_sync(0xffffffffu, eq)) - 1;
+}
+
+// ---- push-based exchange inside a cluster ---------------------------------------
+__device__ __forceinline__ void mbar_init_(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (about one second); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1;; ++i) {
+        if (mbar_try(a, parity)) return true;
+        if ((i & 255) == 0 && (global_ns() - t0 > 1000000000ULL || i > (1LL << 30))) return false;
+    }
+}
+// 16 bytes to the shared memory of another CTA of the cluster, counted on its mbarrier.
+__device__ __forceinline__ void push16(uint32_t raddr, uint4 v, uint32_t rmbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(raddr),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rmbar)
+                 : "memory");
+}
+
+template <typename T, int NB>
+struct __align__(16) Slot {  // one published row: key, origin, values (padded for shifted reads)
+    Cand<T> key;
+    int orig;
+    alignas(16) T row[2 * NB];
+};
 
 template <typename T, int NB, int NT, int RPT>
 struct PanelSmem {
-    T fin[NT * RPT][NB + 1];        // finished values of the local rows (natural column order;
-                                    // odd row stride: consecutive rows fall in different banks)
-    T crow[2][NB];                  // this CTA's candidate row (double-buffered: read remotely)
-    T drow[2][NB];                  // the diagonal row, if this CTA holds it
-    __align__(16) T prow_s[2 * NB]; // pivot row in shifted coordinates: prow_s[t] = pivot[j + t]
-    T prow[NB];                     // pivot row, natural columns
-    T orow[NB];                     // old diagonal row, natural columns
+    T fin[NT * RPT][NB + 1];   // finished values of the local rows (natural column order;
+                               // odd row stride: consecutive rows fall in different banks)
+    Slot<T, NB> rc[2][16];     // candidates received from every CTA (double-buffered by column)
+    Slot<T, NB> rd[2];         // the diagonal row
+    Slot<T, NB> stage[2];      // this CTA's outgoing candidate / diagonal row
+    uint64_t mbar[2];
     Cand<T> wkey[NT / 32];
-    Cand<T> ckey[2];
-    int corig[2];
-    int dorig[2];
-    int cidx, p, porig, dorg;
+    alignas(16) T wsh[NT / 32][NB];  // per-warp shifted pivot row
 };
 
 template <typename T, int NB, int RPT, int NT>
@@ -104,16 +159,28 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                    int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<PanelSmem<T, NB, NT, RPT> *>(smem_raw);
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    constexpr int VW = 16 / sizeof(T);
     constexpr int NW = NT / 32;
+    using SlotT = Slot<T, NB>;
+    constexpr int SLOT_HEAD = (int)offsetof(SlotT, row);  // bytes before the row values
+    constexpr int ROW_BYTES = NB * (int)sizeof(T);
+    static_assert(SLOT_HEAD % 16 == 0 && ROW_BYTES % 16 == 0, "16-byte pushes");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int CL = (int)cluster_nctarank();
     const int rank = (int)cluster_ctarank();
     const int rpc = (m + CL - 1) / CL;
     const int rbase = rank * rpc;
+    const uint32_t bytes_per_col = (uint32_t)(CL + 1) * (SLOT_HEAD + ROW_BYTES);
     if (rank == 0 && tid == 0) *nmoves = 0;
-    for (int t = tid; t < 2 * NB; t += NT) sm.prow_s[t] = T(0);
+    if (CL > 1) {
+        if (tid == 0) {
+            mbar_init_(smem_u32(&sm.mbar[0]), 1);
+            mbar_init_(smem_u32(&sm.mbar[1]), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbar_arm(smem_u32(&sm.mbar[0]), bytes_per_col);  // column 0
+            mbar_arm(smem_u32(&sm.mbar[1]), bytes_per_col);  // column 1
+        }
+        cluster_sync_all();  // every mbarrier is armed before anyone pushes
+    }
 
     T a[RPT][NB];
     int gi[RPT], orig[RPT];
@@ -129,11 +196,12 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
         for (int k = 0; k < NB; ++k) a[s][k] = (valid && k < ncols) ? row[k] : T(0);
     }
 
+    bool ok = true;
     int buf = 0;
 #pragma unroll 1
     for (int j = 0; j < NB; ++j) {
         if (j < ncols) {  // uniform: dead steps only shift
-            // ---- 1. warp candidates
+            // ---- 1. warp candidates -> CTA candidate (every warp reduces)
             Cand<T> c = Cand<T>::none();
 #pragma unroll
             for (int s = 0; s < RPT; ++s)
@@ -144,100 +212,80 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
             c = warp_best(c);
             if (lane == 0) sm.wkey[warp] = c;
             __syncthreads();
-            // ---- 2. the CTA candidate (warp 0)
-            if (warp == 0) {
-                Cand<T> cc = lane < NW ? sm.wkey[lane] : Cand<T>::none();
-                cc = warp_best(cc);
-                if (lane == 0) {
-                    sm.ckey[buf] = cc;
-                    sm.cidx = cc.idx();
+            Cand<T> cc = lane < NW ? sm.wkey[lane] : Cand<T>::none();
+            cc = warp_best(cc);
+            const int ci = cc.idx();
+            const bool holds_diag = j >= rbase && j < rbase + rpc;
+            // ---- 2. publish: the warp holding the CTA candidate (warp 0 if the CTA
+            //         has none) and the warp holding the diagonal row stage their
+            //         rows and push them to every CTA of the cluster
+#pragma unroll
+            for (int which = 0; which < 2; ++which) {
+                int owner_row;
+                if (which == 0) owner_row = ci;
+                else {
+                    if (!holds_diag) continue;
+                    owner_row = j;
                 }
-            }
-            __syncthreads();
-            // ---- 3. publish the CTA candidate row and the diagonal row (only the
-            //         warps that hold them take the branch)
-            const int ci = sm.cidx;
-            bool mine_c = false, mine_d = false;
-#pragma unroll
-            for (int s = 0; s < RPT; ++s) {
-                mine_c |= gi[s] == ci;
-                mine_d |= gi[s] == j;
-            }
-            if (__any_sync(0xffffffffu, mine_c || mine_d)) {
-#pragma unroll
-                for (int s = 0; s < RPT; ++s) {
-                    if (gi[s] == ci) {
-                        const int lrow = tid + s * NT;
-                        for (int k = 0; k < j; ++k) sm.crow[buf][k] = sm.fin[lrow][k];
-#pragma unroll
-                        for (int t = 0; t < NB; ++t)
-                            if (j + t < NB) sm.crow[buf][j + t] = a[s][t];
-                        sm.corig[buf] = orig[s];
-                    }
-                    if (gi[s] == j) {
-                        const int lrow = tid + s * NT;
-                        for (int k = 0; k < j; ++k) sm.drow[buf][k] = sm.fin[lrow][k];
-#pragma unroll
-                        for (int t = 0; t < NB; ++t)
-                            if (j + t < NB) sm.drow[buf][j + t] = a[s][t];
-                        sm.dorig[buf] = orig[s];
-                    }
+                int owarp = 0, os = -1, olane = -1;
+                if (owner_row != INT_MAX) {
+                    const int lr = owner_row - rbase;
+                    owarp = (lr % NT) / 32;
+                    olane = (lr % NT) % 32;
+                    os = lr / NT;
                 }
-            }
-            if (CL > 1) cluster_sync_all(); else __syncthreads();
-            // ---- 4. warp 0 reads the cluster's candidates and fetches the rows
-            if (warp == 0) {
-                Cand<T> g = Cand<T>::none();
-                if (lane < CL) g = (CL > 1) ? Cand<T>::load_remote(mapa_shared(smem_u32(&sm.ckey[buf]), lane))
-                                            : sm.ckey[buf];
-                g = warp_best(g);
-                const int p = g.idx();
-                const int wr = p / rpc;  // CTA holding the pivot row
-                const int dr = j / rpc;  // CTA holding the diagonal row
-                // issue every remote load before using any of them
-                T pv[(NB + 31) / 32], ov[(NB + 31) / 32];
-                int po = 0, dor = 0;
+                if (warp != owarp) continue;
+                Slot<T, NB> &sg = sm.stage[which];
+                if (os >= 0) {
+                    const int lrow = warp * 32 + olane + os * NT;
+                    for (int k = lane; k < j; k += 32) sg.row[k] = sm.fin[lrow][k];
+                    if (lane == olane) {
 #pragma unroll
-                for (int q = 0; q < (NB + 31) / 32; ++q) {
-                    const int k = lane + 32 * q;
-                    if (k < NB) {
-                        if (CL > 1) {
-                            pv[q] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.crow[buf][k]), wr));
-                            ov[q] = ld_dsmem<T>(mapa_shared(smem_u32(&sm.drow[buf][k]), dr));
-                        } else {
-                            pv[q] = sm.crow[buf][k];
-                            ov[q] = sm.drow[buf][k];
+                        for (int s = 0; s < RPT; ++s) {
+                            if (s == os) {  // warp-uniform: os is the same in every lane
+#pragma unroll
+                                for (int t = 0; t < NB; ++t)
+                                    if (j + t < NB) sg.row[j + t] = a[s][t];
+                                sg.orig = orig[s];
+                            }
                         }
+                        sg.key = cc;
                     }
+                } else if (lane == 0) {
+                    sg.key = Cand<T>::none();
+                    sg.orig = -1;
                 }
-                if (lane == 0) {
-                    if (CL > 1) {
-                        po = ld_dsmem_s32(mapa_shared(smem_u32(&sm.corig[buf]), wr));
-                        dor = ld_dsmem_s32(mapa_shared(smem_u32(&sm.dorig[buf]), dr));
-                    } else {
-                        po = sm.corig[buf];
-                        dor = sm.dorig[buf];
+                __syncwarp();
+                // 16-byte chunks: head + row
+                constexpr int CHUNKS = (SLOT_HEAD + ROW_BYTES) / 16;
+                const uint4 *src = reinterpret_cast<const uint4 *>(&sg);
+                if (CL > 1) {
+                    for (int idx = lane; idx < CL * CHUNKS; idx += 32) {
+                        const int dst = idx / CHUNKS, ch = idx - dst * CHUNKS;
+                        const Slot<T, NB> *target = which == 0 ? &sm.rc[buf][rank] : &sm.rd[buf];
+                        const uint32_t raddr = mapa_shared(smem_u32(target) + ch * 16, dst);
+                        const uint32_t rmbar = mapa_shared(smem_u32(&sm.mbar[buf]), dst);
+                        push16(raddr, src[ch], rmbar);
                     }
-                }
-#pragma unroll
-                for (int q = 0; q < (NB + 31) / 32; ++q) {
-                    const int k = lane + 32 * q;
-                    if (k < NB) {
-                        sm.prow[k] = pv[q];
-                        sm.orow[k] = ov[q];
-                        sm.prow_s[k - j + NB] = T(0);  // clear the tail left by earlier columns
-                        if (k >= j) sm.prow_s[k - j] = pv[q];
-                    }
-                }
-                if (lane == 0) {
-                    sm.p = p;
-                    sm.porig = po;
-                    sm.dorg = dor;
+                } else {
+                    uint4 *dstp = reinterpret_cast<uint4 *>(which == 0 ? &sm.rc[buf][0] : &sm.rd[buf]);
+                    for (int ch = lane; ch < CHUNKS; ch += 32) dstp[ch] = src[ch];
                 }
             }
-            __syncthreads();
-            const int p = sm.p;
-            const T piv = sm.prow[j];
+            // ---- 3. wait for the candidates of every CTA and the diagonal row
+            if (CL > 1) {
+                if (!mbar_wait_bounded(smem_u32(&sm.mbar[buf]), (uint32_t)((j >> 1) & 1))) ok = false;
+                __syncwarp();
+            } else {
+                __syncthreads();
+            }
+            const Cand<T> mine = lane < CL ? sm.rc[buf][lane].key : Cand<T>::none();
+            const Cand<T> g = warp_best(mine);
+            const int gw = best_lane(mine, g);
+            const int p = g.idx();
+            const Slot<T, NB> &ps = sm.rc[buf][gw];
+            const Slot<T, NB> &ds = sm.rd[buf];
+            const T piv = ps.row[j];
             if (rank == 0 && tid == 0) {
                 ipiv[j] = row0 + p + 1;
                 if (piv == T(0)) {
@@ -247,27 +295,37 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     mp_flag(st, MP_FLAG_LOWP_BREAKDOWN);
                 }
             }
-            // ---- 5. row exchange (finished part in shared memory, active part in
-            //         registers); only the warps holding row p or row j branch
+            // ---- 4. row exchange; only the warps holding row p or row j branch.
+            //         The finished part is copied by the whole warp.
             bool mine_x = false;
 #pragma unroll
             for (int s = 0; s < RPT; ++s) mine_x |= (gi[s] == p && p != j) || gi[s] == j;
-            if (__any_sync(0xffffffffu, mine_x)) {
+            const unsigned xmask = __ballot_sync(0xffffffffu, mine_x);
+            if (xmask) {
+                // at most two rows change; handle each owner lane in turn
+                unsigned rem = xmask;
+                while (rem) {
+                    const int ol = __ffs(rem) - 1;
+                    rem &= rem - 1;
 #pragma unroll
-                for (int s = 0; s < RPT; ++s) {
-                    const bool is_p = gi[s] == p && p != j;
-                    const bool is_j = gi[s] == j;
-                    if (is_p || is_j) {
-                        const T *src = is_p ? sm.orow : sm.prow;
-                        const int lrow = tid + s * NT;
-                        for (int k = 0; k < j; ++k) sm.fin[lrow][k] = src[k];
+                    for (int s = 0; s < RPT; ++s) {
+                        const int g_s = __shfl_sync(0xffffffffu, gi[s], ol);
+                        const bool is_p = g_s == p && p != j;
+                        const bool is_j = g_s == j;
+                        if (is_p || is_j) {  // warp-uniform
+                            const T *src = is_p ? ds.row : ps.row;
+                            const int lrow = warp * 32 + ol + s * NT;
+                            for (int k = lane; k < j; k += 32) sm.fin[lrow][k] = src[k];
+                            if (lane == ol) {
 #pragma unroll
-                        for (int t = 0; t < NB; ++t) a[s][t] = (j + t < NB) ? src[j + t] : T(0);
-                        orig[s] = is_p ? sm.dorg : sm.porig;
+                                for (int t = 0; t < NB; ++t) a[s][t] = (j + t < NB) ? src[j + t] : T(0);
+                                orig[s] = is_p ? ds.orig : ps.orig;
+                            }
+                        }
                     }
                 }
             }
-            // ---- scale and rank-1 update of the active columns
+            // ---- 5. scale and rank-1 update of the active columns
             T l[RPT];
 #pragma unroll
             for (int s = 0; s < RPT; ++s) {
@@ -278,10 +336,15 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     a[s][0] = l[s];
                 }
             }
-            const V *pr4 = reinterpret_cast<const V *>(sm.prow_s);
+            // the pivot row in shifted coordinates, 16-byte aligned, one copy per warp
+            T *wsh = sm.wsh[warp];
+            for (int t = lane; t < NB; t += 32) wsh[t] = (j + t < NB) ? ps.row[j + t] : T(0);
+            __syncwarp();
+            using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            constexpr int VW = 16 / sizeof(T);
 #pragma unroll
             for (int q = 0; q < NB / VW; ++q) {
-                const V v4 = pr4[q];
+                const V v4 = reinterpret_cast<const V *>(wsh)[q];
                 const T *pv = reinterpret_cast<const T *>(&v4);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
@@ -292,6 +355,10 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     }
                 }
             }
+            // ---- 6. re-arm this buffer for column j + 2: no CTA can push that
+            //         column before it has received our push of column j + 1,
+            //         which comes after every thread here has left column j
+            if (CL > 1 && tid == 0 && j + 2 < ncols) mbar_arm(smem_u32(&sm.mbar[buf]), bytes_per_col);
         }
         // ---- retire column j and shift the active columns
 #pragma unroll
@@ -303,6 +370,7 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
         }
         buf ^= 1;
     }
+    if (!ok) mp_flag(st, MP_FLAG_TIMEOUT);
     __syncthreads();
     // write back the finished rows and the composed permutation
 #pragma unroll
@@ -317,7 +385,7 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
             }
         }
     }
-    // no CTA may leave while a peer can still read its shared memory
+    // no CTA may leave while a peer can still push to it
     if (CL > 1) cluster_sync_all();
 }
 
@@ -354,18 +422,20 @@ cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *i
 
 }  // namespace
 
-// Base panel width for a panel of height m: one CTA keeps 1024 rows (float)
-// of the panel in registers plus the finished part in shared memory, and a
-// cluster has at most 16 CTAs.
+// Base panel width for a panel of height m.  One CTA keeps 1024 rows (512
+// threads x 2 rows) of the active columns in registers and the finished part
+// in shared memory; a cluster has at most 16 CTAs.  Widths are chosen so the
+// register array stays well inside the 128-register budget of a 512-thread
+// CTA (wider rows spill and cost more per column than they save in launches).
 template <>
 int panel_base_width<float>(int m) {
-    if (m <= 16384) return 32;
+    if (m <= 16384) return 24;
     if (m <= 32768) return 16;
     return 8;
 }
 template <>
 int panel_base_width<double>(int m) {
-    if (m <= 16384) return 16;
+    if (m <= 16384) return 8;
     if (m <= 32768) return 8;
     return 4;
 }
@@ -373,14 +443,14 @@ int panel_base_width<double>(int m) {
 template <>
 cudaError_t launch_panel<float>(float *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
                                 int *nmoves, MpDevStatus *st, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<float, 32, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
+    if (m <= 16384) return launch_panel_t<float, 24, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
     if (m <= 32768) return launch_panel_t<float, 16, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
     return launch_panel_t<float, 8, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
 }
 template <>
 cudaError_t launch_panel<double>(double *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
                                  int *nmoves, MpDevStatus *st, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<double, 16, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
+    if (m <= 16384) return launch_panel_t<double, 8, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
     if (m <= 32768) return launch_panel_t<double, 8, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
     return launch_panel_t<double, 4, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
 }
