@@ -132,6 +132,42 @@ MP_API int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const double
                  double *hX, int ldx, int32_t *hipiv, void *work, size_t work_bytes,
                  const mp_opts *opts, mp_stats *stats, void *stream);
 
+/* Symmetric positive definite A (Section 3.1.1: SPOTRF/SPOTRS for the
+ * factorization and solves, DSYMM for the residual; Section 6): factor
+ * A = L L^T at opts->prec from the LOWER triangle of dA (the strict upper
+ * triangle is never read), refine in FP64 with the residual computed from
+ * the lower triangle, or fall back to an FP64 Cholesky solve.  A
+ * non-positive pivot of the low-precision factorization sets
+ * MP_FLAG_LOWP_BREAKDOWN (stats->info = order of the leading minor); if the
+ * FP64 factorization also meets one, the return value is that order (> 0:
+ * A is not positive definite) and X is not a solution.  Arguments as in
+ * mp_gesv without ipiv, numbered 1..13 for the -i error convention. */
+MP_API size_t mp_posv_workspace_bytes(int n, int nrhs, const mp_opts *opts);
+MP_API int mp_posv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+                   int ldx, void *work, size_t work_bytes, const mp_opts *opts, mp_stats *stats,
+                   void *stream);
+
+/* Adjoint of the solve (reverse-mode derivative of X = A^{-1} B; the paper
+ * has no counterpart).  Given the FP64 cotangent G = dL/dX (n x nrhs),
+ * computes Bbar = A^{-T} G (n x nrhs) and Abar = -Bbar X^T (n x n, FP64,
+ * column-major ldab) from the factors that the preceding mp_gesv or mp_posv
+ * call left in `work`: the transposed low-precision solves use W^T (built in
+ * adj_work), and the transposed system is refined in FP64 against A^T by the
+ * Algorithm 1 loop with the same tol/itermax/stall rules (for mp_posv,
+ * A^T = A and the forward factors are used as they are).  work and opts
+ * (prec, nb_outer, allow_fallback) must be those of the forward call, which
+ * must have returned 0, and no other solve may have used `work` since; dX
+ * is the forward solution.  adj_work: mp_gesv_adjoint_workspace_bytes()
+ * (unused after mp_posv, may be NULL then).  stats->flags gets
+ * MP_FLAG_FALLBACK when the forward call's FP64 factors were used and
+ * MP_FLAG_NOT_CONVERGED when the refinement stopped short of tol.
+ * Arguments are numbered 1..19 in order for the -i error convention. */
+MP_API size_t mp_gesv_adjoint_workspace_bytes(int n, const mp_opts *opts);
+MP_API int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
+                           const double *dG, int ldg, double *dBbar, int ldbb, double *dAbar, int ldab,
+                           void *work, size_t work_bytes, void *adj_work, size_t adj_bytes,
+                           const mp_opts *opts, mp_stats *stats, void *stream);
+
 /* Allocation-free variant of mp_gesv (the paper has no counterpart; this is
  * a deployment convenience).  Some callers may not call cudaMalloc: code that
  * runs while a CUDA graph is being captured, services that fix their device
@@ -183,6 +219,16 @@ MP_API int mp_convert(int n, const double *dA, int lda, float *dW, int ldw,
  * (host) has MP_FLAG_LOWP_BREAKDOWN if a pivot was zero or non-finite. */
 MP_API int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp_opts *opts,
                   void *work, size_t work_bytes, int *info, uint32_t *flags, void *stream);
+
+/* In-place Cholesky A = L L^T of the row-major FP32 W (n x n, ldw a multiple
+ * of 32 >= n; only the lower triangle is read), L left in the lower
+ * triangle; the strict upper triangle is used as scratch (its values on
+ * return are unspecified).  Trailing updates A22 -= fl_p(L21) fl_p(L21)^T at
+ * opts->prec (Section 3.1.1, SPOTRF).  On return *info (host) = order of the
+ * first leading minor found not positive (1-based) or 0, and *flags has
+ * MP_FLAG_LOWP_BREAKDOWN in that case.  work: mp_getrf_workspace_bytes(). */
+MP_API int mp_potrf_lowp(int n, float *dW, int ldw, const mp_opts *opts, void *work, size_t work_bytes,
+                         int *info, uint32_t *flags, void *stream);
 
 /* Solve with the FP32 factors (Algorithm 1 steps 5-6):
  * dZ = s * U^{-1} L^{-1} P (dR / s) computed in FP32, s = 2^ceil(log2 ||r||inf)

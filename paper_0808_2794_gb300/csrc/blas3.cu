@@ -190,11 +190,13 @@ struct BatchStride {
     }
 };
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+// TB: B is given transposed (N x K row-major, C -= A B^T).  lower: skip the
+// C tiles strictly above the diagonal (C square, symmetric update).
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TB>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long lda,
             const T *__restrict__ B0, long ldb, T *__restrict__ C0, long ldc, int inner,
-            BatchStride sa, BatchStride sb, BatchStride sc) {
+            BatchStride sa, BatchStride sb, BatchStride sc, int lower) {
     static_assert((BM / TM) * (BN / TN) == 256, "thread layout");
     constexpr int TX = BN / TN;          // threads along N
     constexpr int A_ELEMS = BM * BK / 256;
@@ -208,6 +210,7 @@ gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (lower && n0 > m0 + BM - 1) return;
 
     T ra[A_ELEMS], rb[B_ELEMS];
     auto load_tiles = [&](int k0) {
@@ -220,10 +223,10 @@ gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long
         }
 #pragma unroll
         for (int e = 0; e < B_ELEMS; ++e) {
-            const int lin = tid * B_ELEMS + e;  // contiguous along n within a k-row
-            const int kk = lin / BN, c = lin % BN;
+            const int lin = tid * B_ELEMS + e;  // contiguous along n (along k if TB)
+            const int kk = TB ? lin % BK : lin / BN, c = TB ? lin / BK : lin % BN;
             const int gk = k0 + kk, gc = n0 + c;
-            rb[e] = (gk < K && gc < N) ? B[(long)gk * ldb + gc] : T(0);
+            rb[e] = (gk < K && gc < N) ? (TB ? B[(long)gc * ldb + gk] : B[(long)gk * ldb + gc]) : T(0);
         }
     };
     auto store_tiles = [&](int buf) {
@@ -235,7 +238,8 @@ gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long
 #pragma unroll
         for (int e = 0; e < B_ELEMS; ++e) {
             const int lin = tid * B_ELEMS + e;
-            Bs[buf][lin / BN][lin % BN] = rb[e];
+            if (TB) Bs[buf][lin % BK][lin / BK] = rb[e];
+            else Bs[buf][lin / BN][lin % BN] = rb[e];
         }
     };
 
@@ -291,28 +295,38 @@ gemm_kernel(int M, int N, int K, T alpha, T beta, const T *__restrict__ A0, long
 template <typename T>
 cudaError_t gemm_launch(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,
                         T *C, long ldc, int batch, int inner, BatchStride sa, BatchStride sb, BatchStride sc,
-                        cudaStream_t s);
+                        cudaStream_t s, bool tb = false, int lower = 0);
 
 template <>
 cudaError_t gemm_launch<float>(int M, int N, int K, float alpha, float beta, const float *A, long lda,
                                const float *B, long ldb, float *C, long ldc, int batch, int inner,
-                               BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s) {
+                               BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s, bool tb,
+                               int lower) {
     constexpr int BM = 128, BN = 128, BK = 8;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     mp_note_launch();
-    gemm_kernel<float, BM, BN, BK, 8, 8><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C, ldc,
-                                                              inner, sa, sb, sc);
+    if (tb)
+        gemm_kernel<float, BM, BN, BK, 8, 8, true><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C,
+                                                                        ldc, inner, sa, sb, sc, lower);
+    else
+        gemm_kernel<float, BM, BN, BK, 8, 8, false><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C,
+                                                                         ldc, inner, sa, sb, sc, lower);
     return cudaGetLastError();
 }
 template <>
 cudaError_t gemm_launch<double>(int M, int N, int K, double alpha, double beta, const double *A, long lda,
                                 const double *B, long ldb, double *C, long ldc, int batch, int inner,
-                                BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s) {
+                                BatchStride sa, BatchStride sb, BatchStride sc, cudaStream_t s, bool tb,
+                                int lower) {
     constexpr int BM = 64, BN = 64, BK = 16;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     mp_note_launch();
-    gemm_kernel<double, BM, BN, BK, 4, 4><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C, ldc,
-                                                               inner, sa, sb, sc);
+    if (tb)
+        gemm_kernel<double, BM, BN, BK, 4, 4, true><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C,
+                                                                         ldc, inner, sa, sb, sc, lower);
+    else
+        gemm_kernel<double, BM, BN, BK, 4, 4, false><<<grid, 256, 0, s>>>(M, N, K, alpha, beta, A, lda, B, ldb, C,
+                                                                          ldc, inner, sa, sb, sc, lower);
     return cudaGetLastError();
 }
 
@@ -329,6 +343,18 @@ template cudaError_t launch_gemm_sub<float>(int, int, int, const float *, long, 
                                             long, cudaStream_t);
 template cudaError_t launch_gemm_sub<double>(int, int, int, const double *, long, const double *, long,
                                              double *, long, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_gemm_nt_sub(int M, int N, int K, const T *A, long lda, const T *B, long ldb, T *C, long ldc,
+                               int lower, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    const BatchStride z{0, 0};
+    return gemm_launch<T>(M, N, K, T(-1), T(1), A, lda, B, ldb, C, ldc, 1, 1, z, z, z, s, true, lower);
+}
+template cudaError_t launch_gemm_nt_sub<float>(int, int, int, const float *, long, const float *, long, float *,
+                                               long, int, cudaStream_t);
+template cudaError_t launch_gemm_nt_sub<double>(int, int, int, const double *, long, const double *, long,
+                                                double *, long, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_gemm_batched(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,

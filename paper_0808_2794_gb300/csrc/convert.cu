@@ -60,6 +60,52 @@ convert_transpose_kernel(int n, const double *__restrict__ A, long lda, Tout *__
     }
 }
 
+// Symmetric A given by its lower triangle: W[r][c] = fl(a_rc) for r >= c
+// only (the upper triangle of A is not read and W's is not written).  Row
+// sums of the full symmetric |A|: a strictly-lower a_rc counts for rows r
+// and c.  Grid: one CTA per 32 x 32 tile, tiles above the diagonal exit.
+template <typename Tout>
+__global__ void __launch_bounds__(256)
+convert_lower_kernel(int n, const double *__restrict__ A, long lda, Tout *__restrict__ W, long ldw,
+                     double *__restrict__ rowsum, MpDevStatus *st) {
+    __shared__ Tout tile[kTile][kTile + 1];
+    __shared__ double rs[8][kTile];
+    const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+    if (c0 > r0) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    double rsum = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = c0 + ty + 8 * q, r = r0 + tx;
+        double v = 0.0;
+        if (r < n && c <= r) v = A[(long)c * lda + r];
+        if (!(fabs(v) <= 1.79769313486231570815e308)) bad = true;
+        rsum += fabs(v);
+        // strictly lower entries also count for row c: reduce over the 32 rows r
+        double cs = (r > c) ? fabs(v) : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, off);
+        if (tx == 0 && c < n && cs != 0.0) atomicAdd(&rowsum[c], cs);
+        tile[ty + 8 * q][tx] = cvt<Tout>(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = r0 + ty + 8 * q, c = c0 + tx;
+        if (r < n && c <= r) W[(long)r * ldw + c] = tile[tx][ty + 8 * q];
+    }
+    if (bad) mp_flag(st, MP_FLAG_NONFINITE_INPUT);
+    rs[ty][tx] = rsum;
+    __syncthreads();
+    if (ty == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += rs[q][tx];
+        if (r0 + tx < n && t != 0.0) atomicAdd(&rowsum[r0 + tx], t);
+    }
+}
+
 __global__ void __launch_bounds__(1024) max_reduce_kernel(int n, const double *__restrict__ v, double *out) {
     __shared__ double wm[32];
     double m = 0.0;
@@ -95,6 +141,20 @@ template cudaError_t launch_convert_transpose<float>(int, const double *, long, 
                                                      double *, MpDevStatus *, cudaStream_t);
 template cudaError_t launch_convert_transpose<double>(int, const double *, long, double *, long,
                                                       double *, MpDevStatus *, cudaStream_t);
+
+template <typename Tout>
+cudaError_t launch_convert_lower(int n, const double *A, long lda, Tout *W, long ldw, double *rowsum,
+                                 MpDevStatus *st, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nt = (n + kTile - 1) / kTile;
+    mp_note_launch();
+    convert_lower_kernel<Tout><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(n, A, lda, W, ldw, rowsum, st);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert_lower<float>(int, const double *, long, float *, long, double *,
+                                                 MpDevStatus *, cudaStream_t);
+template cudaError_t launch_convert_lower<double>(int, const double *, long, double *, long, double *,
+                                                  MpDevStatus *, cudaStream_t);
 
 cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s) {
     mp_note_launch();

@@ -42,6 +42,11 @@ template <typename T>
 cudaError_t launch_gemm_batched(int M, int N, int K, T alpha, T beta, const T *A, long lda, const T *B, long ldb,
                                 T *C, long ldc, int batch, int inner, long a_outer, long a_inner, long b_outer,
                                 long b_inner, long c_outer, long c_inner, cudaStream_t s);
+// C[MxN] -= A[MxK] * B[NxK]^T; lower != 0 skips C tiles strictly above the
+// diagonal (C square, symmetric update).
+template <typename T>
+cudaError_t launch_gemm_nt_sub(int M, int N, int K, const T *A, long lda, const T *B, long ldb, T *C, long ldc,
+                               int lower, cudaStream_t s);
 // B[m x N] <- L^{-1} B with L unit lower (m x m, ldl), m <= 64.
 template <typename T>
 cudaError_t launch_trsm_llnu_small(int m, int N, const T *L, long ldl, T *B, long ldb,
@@ -54,6 +59,24 @@ template <typename Tout>
 cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, long ldw,
                                      double *rowsum, MpDevStatus *st, cudaStream_t s);
 cudaError_t launch_max_reduce(int n, const double *v, double *out, cudaStream_t s);
+// Symmetric A by its lower triangle: W[r][c] = fl(a_rc) for r >= c; rowsum
+// of the full symmetric |A| (accumulated, zero first).
+template <typename Tout>
+cudaError_t launch_convert_lower(int n, const double *A, long lda, Tout *W, long ldw, double *rowsum,
+                                 MpDevStatus *st, cudaStream_t s);
+
+// ---- Cholesky (chol.cu) --------------------------------------------------------
+int potrf_leaf_width();
+// Factor columns [k0, k0 + nc) of rows [k0, n) (nc <= potrf_leaf_width()),
+// all earlier updates applied: diagonal block L11 L11^T and L21 = A21 L11^{-T}.
+template <typename T>
+cudaError_t launch_potrf_leaf(int n, int k0, int nc, T *W, long ldw, MpDevStatus *st, cudaStream_t s);
+// Upper triangle of W <- transpose of its strict lower triangle.
+template <typename T>
+cudaError_t launch_mirror_lower(int n, T *W, long ldw, cudaStream_t s);
+// Wt = W^T (n x n, row-major both).
+template <typename T>
+cudaError_t launch_transpose(int n, const T *W, long ldw, T *Wt, long ldwt, cudaStream_t s);
 
 // ---- triangular solves with the factors (trsv.cu) ---------------------------
 // Diagonal blocks of L and U are inverted at block size BI (1024 rows FP32,
@@ -62,8 +85,10 @@ template <typename T> int trsv_inverse_block(int n);
 template <typename T> size_t trsv_inverse_bytes(int n);  // per triangle
 template <typename T> size_t trsv_tmp_bytes(int n);
 template <typename T>
-cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s);
+cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
+                                  bool lower_unit = true, bool upper_unit = false);
 // Lower solve: Y[:,c] = L^{-1} (P r_c) / s_c with r FP64 col-major (ldr), perm
+// (nullptr: identity)
 // the row permutation, s_c = 2^ceil(log2 rnorm[c]).  acc: n*nrhs scratch of T;
 // bar: two unsigned words, zero before first use (a grid barrier).
 template <typename T>
@@ -80,6 +105,11 @@ int residual_ksplit(int n, int nrhs);
 // part[ks][c][i] partial sums of (A X)[i,c] over column chunk ks.
 cudaError_t launch_residual_partial(int n, int nrhs, const double *A, long lda, const double *X,
                                     long ldx, double *part, int ksplit, cudaStream_t s);
+// Symmetric A (lower triangle read): part[K][c][i] = (block column K of A) x_c
+// for K < residual_sym_blocks(n); finalize with ksplit = residual_sym_blocks(n).
+int residual_sym_blocks(int n);
+cudaError_t launch_residual_sym_partial(int n, int nrhs, const double *A, long lda, const double *X, long ldx,
+                                        double *part, cudaStream_t s);
 // R = B - sum_ks part (R = A X when B is null); rnorm[c] = ||R_c||inf,
 // xnorm[c] = ||X_c||inf (zeroed first).
 cudaError_t launch_residual_finalize(int n, int nrhs, const double *part, int ksplit,
@@ -87,9 +117,18 @@ cudaError_t launch_residual_finalize(int n, int nrhs, const double *part, int ks
                                      double *R, long ldr, double *rnorm, double *xnorm,
                                      MpDevStatus *st, cudaStream_t s);
 // X[:,c] (+)= s_c * Z[:,c] with s_c = 2^ceil(log2 rnorm[c]); znorm[c] = ||s_c Z_c||inf.
+// scatter (optional): row i of Z goes to row scatter[i] of X (x = P^T z).
 template <typename T>
 cudaError_t launch_update(int n, int nrhs, const T *Z, long ldz, const double *rnorm, double *X,
-                          long ldx, double *znorm, int assign, cudaStream_t s);
+                          long ldx, double *znorm, int assign, cudaStream_t s, const int *scatter = nullptr);
+// R = G - A^T L (FP64, A column-major n x n: one warp per column of A, fixed
+// summation order); rnorm[c] = ||R_c||inf, xnorm[c] = ||L_c||inf (zeroed first).
+cudaError_t launch_residual_trans(int n, int nrhs, const double *A, long lda, const double *L, long ldl,
+                                  const double *G, long ldg, double *R, long ldr, double *rnorm, double *xnorm,
+                                  MpDevStatus *st, cudaStream_t s);
+// Abar = -L X^T (n x n FP64 column-major), the rank-nrhs outer product of the adjoint.
+cudaError_t launch_outer_neg(int n, int nrhs, const double *L, long ldl, const double *X, long ldx, double *Abar,
+                             long ldab, cudaStream_t s);
 // bnorm[c] = ||B_c||_inf (zeroed first)
 cudaError_t launch_col_absmax(int n, int nrhs, const double *B, long ldb, double *out,
                               MpDevStatus *st, cudaStream_t s);
@@ -102,5 +141,5 @@ cudaError_t launch_project(int n, int k, const double *V, long ldv, const double
 // x += Z[:, 0:k] y; *znorm = max |Z y| (zeroed first)
 cudaError_t launch_correct(int n, int k, const double *Z, long ldz, const double *y, double *x, double *znorm,
                            cudaStream_t s);
-// dst = src / *alpha_inv
-cudaError_t launch_scale(int n, const double *src, const double *alpha_inv, double *dst, cudaStream_t s);
+// dst = src / d
+cudaError_t launch_scale(int n, const double *src, double d, double *dst, cudaStream_t s);

@@ -49,6 +49,7 @@ extern "C" const char *mp_last_error(void) { return g_err; }
 // ---------------------------------------------------------------------------
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 static std::atomic<long long> g_launches{0};
@@ -132,7 +133,14 @@ struct StatusBlock {
     double rnorm[kMaxRhs];
     double xnorm[kMaxRhs];
     double znorm[kMaxRhs];
+    double rr[kMaxRhs];  // ||r_c||_2^2 for the GMRES cycles
+    MpDevStatus gst;     // status sink for the GMRES basis scans (not the input's)
+    int factor_kind;     // factors left in the workspace by the last solve (FactorKind)
+    int pad1;
 };
+
+// What a finished mp_gesv / mp_posv leaves in its workspace, for the adjoint.
+enum FactorKind { kNoFactors = 0, kLuF32 = 1, kLuF64 = 2, kCholF32 = 3, kCholF64 = 4 };
 
 int outer_nb(int n, const mp_opts &o) {
     if (o.nb_outer > 0) return std::max(32, o.nb_outer / 32 * 32);
@@ -145,7 +153,7 @@ int outer_nb(int n, const mp_opts &o) {
 // ---------------------------------------------------------------------------
 struct Layout {
     size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, R, Y, Z,
-        part, tc, total;
+        part, tc, gV, gZ, gsm, total;
     size_t W_bytes;
     int ldw, nblk, ksplit, nb;
 };
@@ -158,7 +166,7 @@ size_t carve(size_t &off, size_t bytes) {
 }
 
 // fp64_space: room for the FP64 fallback (W, inverses, vectors sized for double)
-Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
+Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym = false) {
     Layout L{};
     L.ldw = mp_factor_ld(n);
     L.nblk = (n + 63) / 64;  // blocks of the FP64 solve (the FP32 solve uses half as many)
@@ -185,10 +193,16 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space) {
     L.R = carve(off, sizeof(double) * (size_t)n * rhs);
     L.Y = carve(off, el * (size_t)n * rhs);
     L.Z = carve(off, el * (size_t)n * rhs);
+    if (sym) L.ksplit = residual_sym_blocks(n);  // the symmetric residual's partial sums
     L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
     L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
                                              : std::max(tc_workspace_bytes(n, L.nb, o.prec),
                                                         tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
+    // GMRES: Krylov basis V (m+1 columns), preconditioned vectors Z (m), small vectors
+    const size_t m = o.refine == MP_REFINE_CLASSICAL ? 0 : (size_t)std::max(o.gmres_restart, 1);
+    L.gV = carve(off, m ? sizeof(double) * (size_t)n * (m + 1) : 0);
+    L.gZ = carve(off, sizeof(double) * (size_t)n * m);
+    L.gsm = carve(off, m ? sizeof(double) * (3 * m + 8) : 0);
     L.total = align_up(off, 256);
     return L;
 }
@@ -203,7 +217,6 @@ __global__ void iota_kernel(int *v, int n) {
 }
 cudaError_t launch_iota(int *v, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    mp_note_launch();
     mp_note_launch();
     iota_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, s>>>(v, n);
     return cudaGetLastError();
@@ -325,6 +338,74 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     return cudaSuccess;
 }
 
+// C -= A B^T for the Cholesky updates inside the recursive panel, with the
+// same choice of arithmetic as gemm_fp32_accurate.  lower: only the tiles on
+// or below the diagonal of C (its top square is a diagonal block).
+template <typename T>
+cudaError_t gemm_nt_fp32_accurate(FactorCtx<T> &c, int M, int N, int K, const T *A, long lda, const T *B,
+                                  long ldb, T *C, long ldc, int lower) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (sizeof(T) == 4 && c.prec != MP_PREC_FP32 && (double)M * N * K >= 1.0e8 && lda % 4 == 0 && ldb % 4 == 0)
+        return tc_update_nt(MP_PREC_FP16X3, M, N, K, reinterpret_cast<const float *>(A), lda,
+                            reinterpret_cast<const float *>(B), ldb, reinterpret_cast<float *>(C), ldc, lower, c.tc,
+                            c.st, c.s);
+    return launch_gemm_nt_sub<T>(M, N, K, A, lda, B, ldb, C, ldc, lower, c.s);
+}
+
+// Recursive Cholesky of columns [k0, k0+ncols) of rows [k0, n) (Section
+// 3.1.1, SPOTRF; lower, A = L L^T): left half, then the right half's columns
+// are updated with the left half's L (A -= L_left L_top^T), right half.  A
+// leaf (ncols <= leaf width) factors its diagonal block and solves the rows
+// below it in one launch.
+template <typename T>
+cudaError_t potrf_rec(FactorCtx<T> &c, int k0, int ncols) {
+    const int m = c.n - k0;
+    const int leaf = potrf_leaf_width();
+    T *W = c.W;
+    const long ld = c.ld;
+    if (ncols <= leaf) {
+        MpProfScope ps(MP_KC_PANEL, (double)m * ncols * ncols - 2.0 * ncols * ncols * ncols / 3.0, c.s);
+        return launch_potrf_leaf<T>(c.n, k0, ncols, W, ld, c.st, c.s);
+    }
+    int n1 = (ncols / 2) / leaf * leaf;
+    if (n1 < leaf) n1 = leaf;
+    CU(potrf_rec<T>(c, k0, n1));
+    {
+        MpProfScope ps(MP_KC_PANELGEMM, 2.0 * (m - n1) * (ncols - n1) * n1, c.s);
+        CU(gemm_nt_fp32_accurate<T>(c, m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
+                                    W + (long)(k0 + n1) * ld + k0, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld, 1));
+    }
+    return potrf_rec<T>(c, k0 + n1, ncols - n1);
+}
+
+// Blocked right-looking Cholesky: panel of width nb (recursive), then the
+// trailing update A22 -= fl_p(L21) fl_p(L21)^T on the lower tiles, at
+// precision prec (the symmetric rank-nb update, SSYRK's place in SPOTRF).
+template <typename T>
+cudaError_t potrf_blocked(FactorCtx<T> &c, int nb) {
+    const int n = c.n;
+    T *W = c.W;
+    const long ld = c.ld;
+    for (int k = 0; k < n; k += nb) {
+        const int nbk = std::min(nb, n - k);
+        CU(potrf_rec<T>(c, k, nbk));
+        const int rest = n - k - nbk;
+        if (rest > 0) {
+            MpProfScope ps(MP_KC_UPDATE, (double)rest * rest * nbk, c.s);
+            const T *L21 = W + (long)(k + nbk) * ld + k;
+            T *A22 = W + (long)(k + nbk) * ld + k + nbk;
+            if (sizeof(T) == 4 && c.prec != MP_PREC_FP32) {
+                CU(tc_update_nt(c.prec, rest, rest, nbk, reinterpret_cast<const float *>(L21), ld,
+                                reinterpret_cast<const float *>(L21), ld, reinterpret_cast<float *>(A22), ld, 1,
+                                c.tc, c.st, c.s));
+            } else {
+                CU(launch_gemm_nt_sub<T>(rest, rest, nbk, L21, ld, L21, ld, A22, ld, 1, c.s));
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // the solve
 // ---------------------------------------------------------------------------
@@ -341,6 +422,9 @@ struct Solve {
     cudaStream_t s;
     StatusBlock *sb;
     int epoch;
+    bool sym;    // symmetric positive definite A, lower triangle (Cholesky)
+    bool trans;  // adjoint solve A^T x = b with the transposed LU factors below
+    void *tW, *tLinv, *tUinv;  // W^T (row-major, ld S.L.ldw) and its diagonal-block inverses
 };
 
 int read_status(Solve &S, StatusBlock &h) {
@@ -349,32 +433,59 @@ int read_status(Solve &S, StatusBlock &h) {
     return 0;
 }
 
-// z = U^{-1} L^{-1} P (r / s) in T, from the FP64 R (rnorm gives s); result in S.Z.
+// z = U^{-1} L^{-1} P (r / s) in T for nrhs columns of the FP64 R (rnorm
+// gives s); result in S.Z.
+// With S.trans the factors are those of A^T = U^T L^T P: W^T holds U^T
+// (lower, non-unit) and L^T (upper, unit), the row permutation is applied
+// after the solve (by the update's scatter) instead of before it.
 template <typename T>
-int lowp_solve(Solve &S, const double *R, long ldr, const double *rnorm) {
+int lowp_solve(Solve &S, const double *R, long ldr, const double *rnorm, int nrhs) {
     const Layout &L = S.L;
-    T *W = at<T>(S.work, L.W);
+    T *W = S.trans ? static_cast<T *>(S.tW) : at<T>(S.work, L.W);
+    const T *Linv = S.trans ? static_cast<const T *>(S.tLinv) : at<T>(S.work, L.Linv);
+    const T *Uinv = S.trans ? static_cast<const T *>(S.tUinv) : at<T>(S.work, L.Uinv);
+    const int *perm = S.trans ? nullptr : at<int>(S.work, L.perm);
     ++S.epoch;
-    MpProfScope ps(MP_KC_TRSV, (double)S.n * S.n * sizeof(T) + 4.0 * S.n * S.nrhs * sizeof(T), S.s);
-    MP_CUDA_TRY(launch_trsv_lower<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Linv), R, ldr,
-                                     at<int>(S.work, L.perm), rnorm, at<T>(S.work, L.Y), S.n,
+    MpProfScope ps(MP_KC_TRSV, (double)S.n * S.n * sizeof(T) + 4.0 * S.n * nrhs * sizeof(T), S.s);
+    MP_CUDA_TRY(launch_trsv_lower<T>(S.n, nrhs, W, L.ldw, Linv, R, ldr, perm, rnorm, at<T>(S.work, L.Y), S.n,
                                      at<T>(S.work, L.acc), at<unsigned>(S.work, L.bar), &S.sb->st, S.s));
-    MP_CUDA_TRY(launch_trsv_upper<T>(S.n, S.nrhs, W, L.ldw, at<T>(S.work, L.Uinv), at<T>(S.work, L.Y),
-                                     S.n, at<T>(S.work, L.Z), S.n, at<T>(S.work, L.acc),
-                                     at<unsigned>(S.work, L.bar), &S.sb->st, S.s));
+    MP_CUDA_TRY(launch_trsv_upper<T>(S.n, nrhs, W, L.ldw, Uinv, at<T>(S.work, L.Y), S.n, at<T>(S.work, L.Z), S.n,
+                                     at<T>(S.work, L.acc), at<unsigned>(S.work, L.bar), &S.sb->st, S.s));
+    return 0;
+}
+
+// Row permutation applied to a correction before it is added (adjoint only).
+const int *update_scatter(Solve &S) { return S.trans ? at<int>(S.work, S.L.perm) : nullptr; }
+
+// R = B - A X (R = A X when B is null) for nrhs columns in FP64, with
+// rnorm/xnorm (zeroed by the caller): the general product, or the
+// symmetric one reading the lower triangle of A only.
+int apply_A(Solve &S, int nrhs, const double *X, long ldx, const double *B, long ldb, double *R, long ldr,
+            double *rnorm, double *xnorm, MpDevStatus *st) {
+    const Layout &L = S.L;
+    const double bytes = (S.sym ? 4.0 : 8.0) * S.n * S.n + 32.0 * S.n * nrhs;
+    MpProfScope ps(MP_KC_RESIDUAL, bytes, S.s);
+    int ks;
+    if (S.trans) {  // adjoint: R = B - A^T X, column dots of A (B is never null here)
+        MP_CUDA_TRY(launch_residual_trans(S.n, nrhs, S.A, S.lda, X, ldx, B, ldb, R, ldr, rnorm, xnorm, st, S.s));
+        return 0;
+    }
+    if (S.sym) {
+        ks = residual_sym_blocks(S.n);
+        MP_CUDA_TRY(launch_residual_sym_partial(S.n, nrhs, S.A, S.lda, X, ldx, at<double>(S.work, L.part), S.s));
+    } else {
+        ks = nrhs == S.nrhs ? L.ksplit : residual_ksplit(S.n, nrhs);
+        MP_CUDA_TRY(launch_residual_partial(S.n, nrhs, S.A, S.lda, X, ldx, at<double>(S.work, L.part), ks, S.s));
+    }
+    MP_CUDA_TRY(launch_residual_finalize(S.n, nrhs, at<double>(S.work, L.part), ks, B, ldb, X, ldx, R, ldr, rnorm,
+                                         xnorm, st, S.s));
     return 0;
 }
 
 int residual(Solve &S) {
-    const Layout &L = S.L;
     MP_CUDA_TRY(cudaMemsetAsync(S.sb->rnorm, 0, sizeof(double) * 2 * kMaxRhs, S.s));  // rnorm, xnorm
-    MpProfScope ps(MP_KC_RESIDUAL, 8.0 * S.n * S.n + 32.0 * S.n * S.nrhs, S.s);
-    MP_CUDA_TRY(launch_residual_partial(S.n, S.nrhs, S.A, S.lda, S.X, S.ldx, at<double>(S.work, L.part),
-                                        L.ksplit, S.s));
-    MP_CUDA_TRY(launch_residual_finalize(S.n, S.nrhs, at<double>(S.work, L.part), L.ksplit, S.B, S.ldb,
-                                         S.X, S.ldx, at<double>(S.work, L.R), S.n, S.sb->rnorm,
-                                         S.sb->xnorm, &S.sb->st, S.s));
-    return 0;
+    return apply_A(S, S.nrhs, S.X, S.ldx, S.B, S.ldb, at<double>(S.work, S.L.R), S.n, S.sb->rnorm, S.sb->xnorm,
+                   &S.sb->st);
 }
 
 // Resets the grid-barrier words of the triangular solves.
@@ -395,9 +506,18 @@ int factor(Solve &S, int prec, int nb, int *info_out, uint32_t *flags_out) {
     FactorCtx<T> c{W, (long)L.ldw, S.n, at<int32_t>(S.work, L.ipiv), at<int>(S.work, L.perm),
                    at<int2>(S.work, L.pairs), at<int>(S.work, L.npairs), at<int>(S.work, L.map),
                    &S.sb->st, S.s, prec, at<void>(S.work, L.tc)};
-    MP_CUDA_TRY(getrf_blocked<T>(c, nb));
-    MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
-                                         at<T>(S.work, L.invtmp), S.s));
+    if (S.sym) {
+        // A = L L^T; L^T mirrored into the upper triangle; the lower solve
+        // uses L's own (non-unit) diagonal
+        MP_CUDA_TRY(potrf_blocked<T>(c, nb));
+        MP_CUDA_TRY(launch_mirror_lower<T>(S.n, W, L.ldw, S.s));
+        MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
+                                             at<T>(S.work, L.invtmp), S.s, false));
+    } else {
+        MP_CUDA_TRY(getrf_blocked<T>(c, nb));
+        MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
+                                             at<T>(S.work, L.invtmp), S.s));
+    }
     StatusBlock h;
     int e = read_status(S, h);
     if (e) return e;
@@ -423,10 +543,10 @@ int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *s
     StatusBlock h;
     // steps 2-3: x_0 from b (scaled by 2^ceil(log2 ||b||)); znorm = ||x_0||
     MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
-    int e = lowp_solve<T>(S, S.B, S.ldb, S.sb->bnorm);
+    int e = lowp_solve<T>(S, S.B, S.ldb, S.sb->bnorm, S.nrhs);
     if (e) return e;
     MP_CUDA_TRY(launch_update<T>(S.n, S.nrhs, at<T>(S.work, S.L.Z), S.n, S.sb->bnorm, S.X, S.ldx,
-                                 S.sb->znorm, 1, S.s));
+                                 S.sb->znorm, 1, S.s, update_scatter(S)));
     double zprev[kMaxRhs] = {0};
     int it = 0;
     *conv = false;
@@ -458,11 +578,193 @@ int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *s
         if (it >= itermax) { *conv = all_tol; break; }
         std::memcpy(zprev, h.znorm, sizeof zprev);
         // steps 5-7
-        if ((e = lowp_solve<T>(S, at<double>(S.work, S.L.R), S.n, S.sb->rnorm))) return e;
+        if ((e = lowp_solve<T>(S, at<double>(S.work, S.L.R), S.n, S.sb->rnorm, S.nrhs))) return e;
         MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
         MP_CUDA_TRY(launch_update<T>(S.n, S.nrhs, at<T>(S.work, S.L.Z), S.n, S.sb->rnorm, S.X, S.ldx,
-                                     S.sb->znorm, 0, S.s));
+                                     S.sb->znorm, 0, S.s, update_scatter(S)));
         if (st) st->n_precond += 1;
+        ++it;
+    }
+    *iters = it;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES-based refinement (Section 2.2, Eq. 2; Section 4): the correction
+// equation A d = r is solved by one cycle of right-preconditioned GMRES with
+// M = (LU)^{-1} P from the low-precision factors, in the flexible form that
+// keeps the preconditioned vectors z_k = M v_k (so x += Z y needs no further
+// application of M).  The Arnoldi process runs in FP64 on the device; the
+// (m+1) x m Hessenberg matrix, its Givens rotations and the small triangular
+// solve stay on the host (m <= a few dozen).  Orthogonalisation is classical
+// Gram-Schmidt applied twice (one reduction and one update per pass instead of
+// k dependent ones), which matches modified Gram-Schmidt's loss of
+// orthogonality at O(u) for the basis sizes used here.
+// ---------------------------------------------------------------------------
+struct GmresScratch {
+    double *V, *Z, *h1, *h2, *hh, *vnorm, *tn, *y;
+};
+
+GmresScratch gmres_scratch(Solve &S, int m) {
+    double *g = at<double>(S.work, S.L.gsm);
+    GmresScratch G;
+    G.V = at<double>(S.work, S.L.gV);
+    G.Z = at<double>(S.work, S.L.gZ);
+    G.h1 = g;
+    G.h2 = g + (m + 1);
+    G.hh = g + 2 * (m + 1);
+    G.vnorm = G.hh + 1;
+    G.tn = G.vnorm + 1;  // two scratch norms of A z
+    G.y = G.tn + 2;      // m entries
+    return G;
+}
+
+// One GMRES cycle on A d = r_c (r_c = column c of the FP64 residual in
+// S.L.R, beta = ||r_c||_2 > 0); applies x_c += Z y and leaves ||Z y||inf in
+// sb->znorm[c] (zeroed by the caller).  *steps = inner steps taken; *bad is
+// set when the Arnoldi process produced a non-finite value.
+// The inner loop stops once the least-squares residual |g_k| is below
+// gmres_tol * beta or below sqrt(n) u64 ||A||inf ||x_c||inf (floor), the
+// level at which r itself is known.
+template <typename T>
+int gmres_cycle(Solve &S, const mp_opts &o, int c, double beta, double floor, int *steps, bool *bad) {
+    const int n = S.n, m = o.gmres_restart;
+    const long ldm = n;
+    GmresScratch G = gmres_scratch(S, m);
+    const double *r = at<double>(S.work, S.L.R) + (long)c * n;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hb(2 * (m + 1) + 1);
+    auto Hk = [&](int i, int j) -> double & { return H[(size_t)j * (m + 1) + i]; };
+    g[0] = beta;
+    *bad = false;
+    MP_CUDA_TRY(launch_scale(n, r, beta, G.V, S.s));
+    int k = 0;
+    while (k < m) {
+        double *vk = G.V + k * ldm, *w = G.V + (k + 1) * ldm, *zk = G.Z + k * ldm;
+        // z_k = M v_k: the low-precision solve, v_k scaled by 2^ceil(log2 ||v_k||inf)
+        MP_CUDA_TRY(cudaMemsetAsync(G.vnorm, 0, 3 * sizeof(double), S.s));
+        MP_CUDA_TRY(launch_col_absmax(n, 1, vk, ldm, G.vnorm, &S.sb->gst, S.s));
+        int e = lowp_solve<T>(S, vk, ldm, G.vnorm, 1);
+        if (e) return e;
+        MP_CUDA_TRY(launch_update<T>(n, 1, at<T>(S.work, S.L.Z), n, G.vnorm, zk, ldm, G.tn, 1, S.s));
+        // w = A z_k in FP64
+        MP_CUDA_TRY(cudaMemsetAsync(G.tn, 0, 2 * sizeof(double), S.s));
+        if ((e = apply_A(S, 1, zk, ldm, nullptr, 0, w, ldm, G.tn, G.tn + 1, &S.sb->gst))) return e;
+        // two passes of classical Gram-Schmidt against v_0..v_k, then ||w||_2^2
+        MP_CUDA_TRY(launch_dots(n, k + 1, G.V, ldm, w, G.h1, S.s));
+        MP_CUDA_TRY(launch_project(n, k + 1, G.V, ldm, G.h1, w, S.s));
+        MP_CUDA_TRY(launch_dots(n, k + 1, G.V, ldm, w, G.h2, S.s));
+        MP_CUDA_TRY(launch_project(n, k + 1, G.V, ldm, G.h2, w, S.s));
+        MP_CUDA_TRY(launch_dots(n, 1, w, ldm, w, G.hh, S.s));
+        MP_CUDA_TRY(cudaMemcpyAsync(hb.data(), G.h1, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+        MP_CUDA_TRY(cudaStreamSynchronize(S.s));
+        for (int j = 0; j <= k; ++j) Hk(j, k) = hb[j] + hb[(m + 1) + j];
+        const double hn = std::sqrt(hb[2 * (m + 1)]);
+        Hk(k + 1, k) = hn;
+        if (!std::isfinite(hn)) { *bad = true; break; }
+        // earlier rotations on column k, then a new one zeroing H(k+1, k)
+        for (int j = 0; j < k; ++j) {
+            const double a = Hk(j, k), b = Hk(j + 1, k);
+            Hk(j, k) = cs[j] * a + sn[j] * b;
+            Hk(j + 1, k) = -sn[j] * a + cs[j] * b;
+        }
+        const double a = Hk(k, k), b = Hk(k + 1, k), den = std::hypot(a, b);
+        cs[k] = den == 0.0 ? 1.0 : a / den;
+        sn[k] = den == 0.0 ? 0.0 : b / den;
+        Hk(k, k) = cs[k] * a + sn[k] * b;
+        Hk(k + 1, k) = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        ++k;
+        // |g_{k}| is the residual norm of the small least-squares problem
+        if (std::fabs(g[k]) <= std::max(o.gmres_tol * beta, floor) || hn == 0.0) break;
+        MP_CUDA_TRY(launch_scale(n, w, hn, w, S.s));
+    }
+    *steps = k;
+    if (*bad) return 0;
+    // y = R_k^{-1} g_k (back substitution), then x_c += Z y
+    std::vector<double> y(std::max(k, 1), 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int j = i + 1; j < k; ++j) t -= Hk(i, j) * y[j];
+        y[i] = Hk(i, i) != 0.0 ? t / Hk(i, i) : 0.0;
+        if (!std::isfinite(y[i])) *bad = true;
+    }
+    if (*bad || k == 0) return 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(G.y, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, S.s));
+    MP_CUDA_TRY(launch_correct(n, k, G.Z, ldm, G.y, S.X + (long)c * S.ldx, &S.sb->znorm[c], S.s));
+    return 0;
+}
+
+// Outer FP64 loop of GMRES-based refinement.  Starts from x_0 = M b unless
+// from_x (then from the X the classical loop left).  Per column the
+// acceptance rule of the classical loop (bwd <= tol at the FP64 floor), where
+// the floor is also reached once ||r||_2 <= 4 sqrt(n) u64 ||A||inf ||x||inf
+// (the residual is rounding noise); outer steps with no shrink of the
+// correction and bwd > tol are a stall.
+template <typename T>
+int refine_gmres(Solve &S, const mp_opts &o, bool from_x, mp_stats *st, bool *conv, int *iters,
+                 uint32_t *flags) {
+    StatusBlock h;
+    int e;
+    *conv = false;
+    *flags |= MP_FLAG_GMRES_USED;
+    if (!from_x) {
+        MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
+        if ((e = lowp_solve<T>(S, S.B, S.ldb, S.sb->bnorm, S.nrhs))) return e;
+        MP_CUDA_TRY(launch_update<T>(S.n, S.nrhs, at<T>(S.work, S.L.Z), S.n, S.sb->bnorm, S.X, S.ldx,
+                                     S.sb->znorm, 1, S.s));
+        if (st) st->n_precond += 1;
+    }
+    double zprev[kMaxRhs] = {0};
+    bool cdone[kMaxRhs] = {false};
+    int it = 0;
+    const double u64 = 1.1102230246251565e-16;
+    for (;;) {
+        if ((e = residual(S))) return e;
+        for (int c = 0; c < S.nrhs; ++c)
+            MP_CUDA_TRY(launch_dots(S.n, 1, at<double>(S.work, S.L.R) + (long)c * S.n, S.n,
+                                    at<double>(S.work, S.L.R) + (long)c * S.n, &S.sb->rr[c], S.s));
+        if ((e = read_status(S, h))) return e;
+        double worst = 0.0;
+        bool done = true, nonfinite = false, stalled = false, all_tol = true;
+        for (int c = 0; c < S.nrhs; ++c) {
+            const double b = bwd_of(h, c);
+            const bool stagnant = it >= 2 && h.znorm[c] > o.stall_ratio * zprev[c];
+            // a residual at the level at which it can be computed also marks
+            // the floor: no GMRES cycle can determine a correction from it
+            const bool r_floor = std::sqrt(h.rr[c]) <= 4.0 * std::sqrt((double)S.n) * u64 * h.st.anorm * h.xnorm[c];
+            const bool at_floor = b == 0.0 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant || r_floor;
+            cdone[c] = b <= o.tol && at_floor;
+            if (!(b <= o.tol)) all_tol = false;
+            if (!cdone[c]) done = false;
+            if (!(b <= o.tol) && stagnant) stalled = true;
+            if (!(b == b) || std::isinf(b)) nonfinite = true;
+            worst = std::max(worst, std::isnan(b) ? INFINITY : b);
+        }
+        if (st) {
+            if (st->nhist < 32) st->hist[st->nhist++] = worst;
+            st->bwd_err = worst;
+        }
+        *flags |= h.st.flags & (MP_FLAG_TIMEOUT | MP_FLAG_NONFINITE_INPUT);
+        if (h.st.flags & MP_FLAG_TIMEOUT) break;
+        if (nonfinite) { *flags |= MP_FLAG_LOWP_BREAKDOWN; break; }
+        if (done) { *conv = true; break; }
+        if (stalled) { *flags |= MP_FLAG_STALLED; break; }
+        if (it >= o.itermax) { *conv = all_tol; break; }
+        std::memcpy(zprev, h.znorm, sizeof zprev);
+        MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, S.s));
+        bool bad = false;
+        for (int c = 0; c < S.nrhs; ++c) {
+            const double beta = std::sqrt(h.rr[c]);
+            if (cdone[c] || !(beta > 0.0)) continue;
+            int steps = 0;
+            bool badc = false;
+            const double floor = std::sqrt((double)S.n) * u64 * h.st.anorm * h.xnorm[c];
+            if ((e = gmres_cycle<T>(S, o, c, beta, floor, &steps, &badc))) return e;
+            if (st) st->n_precond += steps;
+            bad = bad || badc;
+        }
+        if (bad) { *flags |= MP_FLAG_LOWP_BREAKDOWN; break; }
         ++it;
     }
     *iters = it;
@@ -472,6 +774,10 @@ int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *s
 int validate_opts(const mp_opts &o) {
     if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_FP16) return 1;
     if (o.itermax < 0 || !(o.tol > 0.0) || o.stall_ratio <= 0.0) return 1;
+    if (o.refine < MP_REFINE_CLASSICAL || o.refine > MP_REFINE_AUTO) return 1;
+    if (o.refine != MP_REFINE_CLASSICAL &&
+        (o.gmres_restart < 1 || o.gmres_restart > 128 || !(o.gmres_tol > 0.0) || !(o.gmres_tol < 1.0)))
+        return 1;
     return 0;
 }
 
@@ -494,12 +800,15 @@ extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double 
                         stats != nullptr);
 }
 
-int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
-                 int ldx, int32_t *dipiv, void *work, size_t work_bytes, const mp_opts *opts,
-                 mp_stats *stats, void *stream, bool timing) {
+// The driver behind mp_gesv (sym = false: PA = LU) and mp_posv (sym = true:
+// A = L L^T from the lower triangle; no ipiv, arguments numbered without it).
+int solve_impl(bool sym, int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+               int ldx, int32_t *dipiv, void *work, size_t work_bytes, const mp_opts *opts, mp_stats *stats,
+               void *stream, bool timing) {
     g_err[0] = 0;
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
+    const int after = sym ? 1 : 0;  // arguments after ipiv shift down by one for posv
     if (n < 0) return mp_arg_fail(1, "n < 0");
     if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
     if (n > 65536) return mp_arg_fail(1, "n > 65536 is not supported");
@@ -509,30 +818,34 @@ int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, i
     if (ldb < std::max(1, n)) return mp_arg_fail(6, "ldb < max(1, n)");
     if (n > 0 && nrhs > 0 && !dX) return mp_arg_fail(7, "X is NULL");
     if (ldx < std::max(1, n)) return mp_arg_fail(8, "ldx < max(1, n)");
-    if (n > 0 && !dipiv) return mp_arg_fail(9, "ipiv is NULL");
-    if (validate_opts(o)) return mp_arg_fail(12, "invalid options");
+    if (!sym && n > 0 && !dipiv) return mp_arg_fail(9, "ipiv is NULL");
+    if (validate_opts(o)) return mp_arg_fail(12 - after, "invalid options");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
     }
     if (n == 0 || nrhs == 0) return 0;
     const bool fb = o.allow_fallback != 0;
-    Layout L = make_layout(n, nrhs, o, fb);
-    if (!work) return mp_arg_fail(10, "workspace is NULL");
-    if (work_bytes < L.total) return mp_arg_fail(11, "workspace too small");
+    Layout L = make_layout(n, nrhs, o, fb, sym);
+    if (!work) return mp_arg_fail(10 - after, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(11 - after, "workspace too small");
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Solve S{n, nrhs, dA, lda, dB, ldb, dX, ldx, work, L, s, at<StatusBlock>(work, L.status), 0};
+    Solve S{n, nrhs, dA, lda, dB, ldb, dX, ldx, work, L, s, at<StatusBlock>(work, L.status), 0, sym};
     cudaEvent_t ev[5] = {};
     if (timing)
         for (auto &e : ev) MP_CUDA_TRY(cudaEventCreate(&e));
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+    auto convert = [&](auto *W) -> cudaError_t {
+        using T = std::remove_pointer_t<decltype(W)>;
+        return sym ? launch_convert_lower<T>(n, dA, lda, W, L.ldw, at<double>(work, L.rowsum), &S.sb->st, s)
+                   : launch_convert_transpose<T>(n, dA, lda, W, L.ldw, at<double>(work, L.rowsum), &S.sb->st, s);
+    };
 
     mark(0);
     MP_CUDA_TRY(cudaMemsetAsync(S.sb, 0, sizeof(StatusBlock), s));
     MP_CUDA_TRY(cudaMemsetAsync(at<double>(work, L.rowsum), 0, sizeof(double) * n, s));
     if (reset_sync(S)) return -1000;
-    MP_CUDA_TRY(launch_convert_transpose<float>(n, dA, lda, at<float>(work, L.W), L.ldw,
-                                                at<double>(work, L.rowsum), &S.sb->st, s));
+    MP_CUDA_TRY(convert(at<float>(work, L.W)));
     MP_CUDA_TRY(launch_max_reduce(n, at<double>(work, L.rowsum), &S.sb->st.anorm, s));
     MP_CUDA_TRY(launch_col_absmax(n, nrhs, dB, ldb, S.sb->bnorm, &S.sb->st, s));
     mark(1);
@@ -545,20 +858,30 @@ int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, i
     mark(2);
     flags |= fflags & (MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT);
     if (!(flags & (MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT))) {
-        if ((e = refine<float>(S, o, o.itermax, true, stats, &conv, &iters, &flags))) return e;
+        if (o.refine == MP_REFINE_GMRES) {
+            if ((e = refine_gmres<float>(S, o, false, stats, &conv, &iters, &flags))) return e;
+        } else {
+            if ((e = refine<float>(S, o, o.itermax, true, stats, &conv, &iters, &flags))) return e;
+            // AUTO: a classical loop that stalled or ran out of corrections
+            // continues with GMRES on the same factors (Section 2.2)
+            const uint32_t hard = MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT | MP_FLAG_TIMEOUT;
+            if (!conv && o.refine == MP_REFINE_AUTO && !(flags & hard)) {
+                int itg = 0;
+                if ((e = refine_gmres<float>(S, o, true, stats, &conv, &itg, &flags))) return e;
+                iters += itg;
+            }
+        }
     }
     if (stats) stats->info = info;
     mark(3);
     int ret = 0;
     if (!conv && fb && !(flags & MP_FLAG_NONFINITE_INPUT)) {
-        // Section 4: resort to the double-precision solver (FP64 LU on the GPU)
-        Layout L64 = L;
-        S.L = L64;
+        // Section 4: resort to the double-precision solver (FP64 LU or
+        // Cholesky on the GPU, the same kernels instantiated for FP64)
         MP_CUDA_TRY(cudaMemsetAsync(&S.sb->st.zero_pivot, 0, sizeof(int), s));
         MP_CUDA_TRY(cudaMemsetAsync(&S.sb->st.flags, 0, sizeof(uint32_t), s));
         if (reset_sync(S)) return -1000;
-        MP_CUDA_TRY(launch_convert_transpose<double>(n, dA, lda, at<double>(work, L.W), L.ldw,
-                                                     at<double>(work, L.rowsum), &S.sb->st, s));
+        MP_CUDA_TRY(convert(at<double>(work, L.W)));
         int info64 = 0;
         uint32_t f64 = 0;
         if ((e = factor<double>(S, MP_PREC_FP32, std::min(L.nb, 256), &info64, &f64))) return e;
@@ -581,8 +904,15 @@ int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, i
     } else if (!conv) {
         flags |= MP_FLAG_NOT_CONVERGED;
     }
-    MP_CUDA_TRY(cudaMemcpyAsync(dipiv, at<int32_t>(work, L.ipiv), sizeof(int32_t) * n,
-                                cudaMemcpyDeviceToDevice, s));
+    if (!sym)
+        MP_CUDA_TRY(cudaMemcpyAsync(dipiv, at<int32_t>(work, L.ipiv), sizeof(int32_t) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+    {
+        // the factors now in the workspace, for mp_gesv_adjoint
+        const bool f64 = (flags & MP_FLAG_FALLBACK) != 0;
+        const int kind = ret != 0 ? kNoFactors : sym ? (f64 ? kCholF64 : kCholF32) : (f64 ? kLuF64 : kLuF32);
+        MP_CUDA_TRY(cudaMemcpyAsync(&S.sb->factor_kind, &kind, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     mark(4);
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     if (stats) {
@@ -598,6 +928,143 @@ int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, i
     if (timing)
         for (auto &ev_ : ev) cudaEventDestroy(ev_);
     return ret;
+}
+
+int mp_gesv_impl(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+                 int ldx, int32_t *dipiv, void *work, size_t work_bytes, const mp_opts *opts,
+                 mp_stats *stats, void *stream, bool timing) {
+    return solve_impl(false, n, nrhs, dA, lda, dB, ldb, dX, ldx, dipiv, work, work_bytes, opts, stats, stream,
+                      timing);
+}
+
+extern "C" size_t mp_posv_workspace_bytes(int n, int nrhs, const mp_opts *opts) {
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0 || nrhs < 0) return 0;
+    return make_layout(n, nrhs, o, o.allow_fallback != 0, true).total;
+}
+
+extern "C" int mp_posv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+                       int ldx, void *work, size_t work_bytes, const mp_opts *opts, mp_stats *stats,
+                       void *stream) {
+    return solve_impl(true, n, nrhs, dA, lda, dB, ldb, dX, ldx, nullptr, work, work_bytes, opts, stats, stream,
+                      stats != nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the solve (the reverse-mode derivative of X = A^{-1} B; not in
+// the paper): Bbar = A^{-T} G by transposed solves with the factors the
+// forward call left in its workspace, refined in FP64 against A^T exactly as
+// Algorithm 1 refines against A, then Abar = -Bbar X^T.
+// ---------------------------------------------------------------------------
+namespace {
+struct AdjLayout {
+    size_t Wt, Linv, Uinv, tmp, total;
+};
+AdjLayout adj_layout(int n, bool fp64) {
+    AdjLayout L{};
+    const size_t el = fp64 ? sizeof(double) : sizeof(float);
+    size_t off = 0;
+    L.Wt = carve(off, (size_t)n * (size_t)mp_factor_ld(n) * el);
+    const size_t inv = std::max(trsv_inverse_bytes<float>(n), fp64 ? trsv_inverse_bytes<double>(n) : 0);
+    L.Linv = carve(off, inv);
+    L.Uinv = carve(off, inv);
+    L.tmp = carve(off, std::max(trsv_tmp_bytes<float>(n), fp64 ? trsv_tmp_bytes<double>(n) : 0));
+    L.total = align_up(off, 256);
+    return L;
+}
+
+template <typename T>
+int adjoint_solve(Solve &S, const mp_opts &o, void *adj, const AdjLayout &AL, mp_stats *st, bool *conv, int *iters,
+                  uint32_t *flags) {
+    if (!S.sym) {
+        // A^T = U^T L^T P: W^T has U^T in its lower triangle, L^T (unit) in its upper
+        T *W = at<T>(S.work, S.L.W);
+        T *Wt = at<T>(adj, AL.Wt);
+        MP_CUDA_TRY(launch_transpose<T>(S.n, W, S.L.ldw, Wt, S.L.ldw, S.s));
+        MP_CUDA_TRY(launch_build_inverses<T>(S.n, Wt, S.L.ldw, at<T>(adj, AL.Linv), at<T>(adj, AL.Uinv),
+                                             at<T>(adj, AL.tmp), S.s, false, true));
+        S.trans = true;
+        S.tW = Wt;
+        S.tLinv = at<T>(adj, AL.Linv);
+        S.tUinv = at<T>(adj, AL.Uinv);
+    }
+    // (for Cholesky A^T = A: the forward factors serve unchanged)
+    return refine<T>(S, o, o.itermax, true, st, conv, iters, flags);
+}
+}  // namespace
+
+extern "C" size_t mp_gesv_adjoint_workspace_bytes(int n, const mp_opts *opts) {
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0) return 0;
+    return adj_layout(n, o.allow_fallback != 0).total;
+}
+
+extern "C" int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
+                               const double *dG, int ldg, double *dBbar, int ldbb, double *dAbar, int ldab,
+                               void *work, size_t work_bytes, void *adj_work, size_t adj_bytes,
+                               const mp_opts *opts, mp_stats *stats, void *stream) {
+    g_err[0] = 0;
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 65536) return mp_arg_fail(1, "n > 65536 is not supported");
+    if (n > 0 && !dA) return mp_arg_fail(3, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(4, "lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dX) return mp_arg_fail(5, "X is NULL");
+    if (ldx < std::max(1, n)) return mp_arg_fail(6, "ldx < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dG) return mp_arg_fail(7, "G is NULL");
+    if (ldg < std::max(1, n)) return mp_arg_fail(8, "ldg < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dBbar) return mp_arg_fail(9, "Bbar is NULL");
+    if (ldbb < std::max(1, n)) return mp_arg_fail(10, "ldbb < max(1, n)");
+    if (ldab < std::max(1, n)) return mp_arg_fail(12, "ldab < max(1, n)");
+    if (validate_opts(o)) return mp_arg_fail(17, "invalid options");
+    o.refine = MP_REFINE_CLASSICAL;  // the transposed system is refined by Algorithm 1
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n == 0) return 0;
+    if (!work) return mp_arg_fail(13, "workspace is NULL");
+    if (work_bytes < sizeof(StatusBlock)) return mp_arg_fail(14, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = static_cast<StatusBlock *>(work);  // first region of every solve layout
+    int kind = 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(&kind, &sb->factor_kind, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (kind == kNoFactors || kind > kCholF64)
+        return mp_arg_fail(13, "workspace holds no factors of a finished mp_gesv / mp_posv");
+    const bool sym = kind == kCholF32 || kind == kCholF64;
+    const bool f64 = kind == kLuF64 || kind == kCholF64;
+    Layout L = make_layout(n, std::max(nrhs, 1), o, o.allow_fallback != 0, sym);
+    if (work_bytes < L.total) return mp_arg_fail(14, "workspace too small for (n, nrhs, opts)");
+    if (f64 && !o.allow_fallback) return mp_arg_fail(17, "FP64 factors need allow_fallback = 1 in opts");
+    AdjLayout AL = adj_layout(n, o.allow_fallback != 0);
+    if (!sym && !adj_work) return mp_arg_fail(15, "adjoint workspace is NULL");
+    if (!sym && adj_bytes < AL.total) return mp_arg_fail(16, "adjoint workspace too small");
+    if (nrhs == 0) return 0;
+    if (!dAbar) return mp_arg_fail(11, "Abar is NULL");
+
+    Solve S{n, nrhs, dA, lda, dG, ldg, dBbar, ldbb, work, L, s, sb, 0, sym};
+    // status words of this solve (the factor record stays)
+    MP_CUDA_TRY(cudaMemsetAsync(&sb->st.flags, 0, sizeof(uint32_t), s));
+    MP_CUDA_TRY(cudaMemsetAsync(sb->bnorm, 0, sizeof(double) * kMaxRhs, s));
+    if (reset_sync(S)) return -1000;
+    MP_CUDA_TRY(launch_col_absmax(n, nrhs, dG, ldg, sb->bnorm, &sb->st, s));
+    bool conv = false;
+    int iters = 0, e;
+    uint32_t flags = 0;
+    if (f64) e = adjoint_solve<double>(S, o, adj_work, AL, stats, &conv, &iters, &flags);
+    else e = adjoint_solve<float>(S, o, adj_work, AL, stats, &conv, &iters, &flags);
+    if (e) return e;
+    if (!conv) flags |= MP_FLAG_NOT_CONVERGED;
+    if (f64) flags |= MP_FLAG_FALLBACK;
+    MP_CUDA_TRY(launch_outer_neg(n, nrhs, dBbar, ldbb, dX, ldx, dAbar, ldab, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iter = iters;
+        stats->flags = flags;
+    }
+    return 0;
 }
 
 extern "C" size_t mp_gesv_host_workspace_bytes(int n, int nrhs, const mp_opts *opts) {
@@ -748,6 +1215,36 @@ extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp
     FactorCtx<float> c{dW, (long)ldw, n, dipiv, at<int>(work, L.perm), at<int2>(work, L.pairs),
                        at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc)};
     MP_CUDA_TRY(getrf_blocked<float>(c, nb));
+    StatusBlock h;
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (info) *info = h.st.zero_pivot;
+    if (flags) *flags = h.st.flags;
+    return 0;
+}
+
+extern "C" int mp_potrf_lowp(int n, float *dW, int ldw, const mp_opts *opts, void *work, size_t work_bytes,
+                             int *info, uint32_t *flags, void *stream) {
+    g_err[0] = 0;
+    mp_opts o;
+    if (opts) o = *opts; else mp_default_opts(&o);
+    if (n < 0 || n > 65536) return mp_arg_fail(1, "n out of range [0, 65536]");
+    if (n > 0 && !dW) return mp_arg_fail(2, "W is NULL");
+    if (ldw < mp_factor_ld(n) || ldw % 32) return mp_arg_fail(3, "ldw must be a multiple of 32 >= n");
+    if (validate_opts(o)) return mp_arg_fail(4, "invalid options");
+    const int nb = outer_nb(n, o);
+    StepLayout L = step_layout(n, 1, nb, o.prec);
+    if (!work) return mp_arg_fail(5, "workspace is NULL");
+    if (work_bytes < L.total) return mp_arg_fail(6, "workspace too small");
+    if (info) *info = 0;
+    if (flags) *flags = 0;
+    if (n == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusBlock *sb = at<StatusBlock>(work, L.status);
+    MP_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(StatusBlock), s));
+    FactorCtx<float> c{dW, (long)ldw, n, nullptr, at<int>(work, L.perm), at<int2>(work, L.pairs),
+                       at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc)};
+    MP_CUDA_TRY(potrf_blocked<float>(c, nb));
     StatusBlock h;
     MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));
     MP_CUDA_TRY(cudaStreamSynchronize(s));

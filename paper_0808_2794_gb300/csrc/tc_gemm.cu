@@ -160,7 +160,7 @@ template <uint32_t FMT, int SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float *__restrict__ C, long ldc, int M, int N, int KB, int a_lo_row, int b_lo_row,
-                 const float *__restrict__ inv_scale_p, MpDevStatus *st) {
+                 const float *__restrict__ inv_scale_p, MpDevStatus *st, int lower) {
     constexpr int STAGES = TcCfg<SPLIT>::STAGES;
     constexpr int STAGE_BYTES = TcCfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smem_raw[];
@@ -171,6 +171,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     const int num_i = (M + TILE_I - 1) / TILE_I;
     const int num_j = (N + TILE_J - 1) / TILE_J;
     const int ntiles = num_i * num_j;
+    // lower: tiles whose columns all lie right of their rows are skipped
+    // (every role walks the same tile sequence, so the pipelines stay paired)
+    auto skip = [&](int t) { return lower && (t / num_i) * TILE_J > (t % num_i) * TILE_I + TILE_I - 1; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -201,6 +204,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             int stage = 0;
             uint32_t phase = 0;
             for (int t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
+                if (skip(t)) continue;
                 const int ib = t % num_i, jb = t / num_i;
                 for (int kb = 0; kb < KB; ++kb) {
                     if (!mbar_wait(smem_u32(&bar->empty[stage]), phase ^ 1u, abort_flag)) { timed_out = true; break; }
@@ -224,6 +228,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             uint32_t phase = 0, acc_phase = 0;
             int acc = 0;
             for (int t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
+                if (skip(t)) continue;
                 if (!mbar_wait(smem_u32(&bar->tempty[acc]), acc_phase ^ 1u, abort_flag)) { timed_out = true; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)acc * TILE_I;
@@ -257,6 +262,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (skip(t)) continue;
             const int ib = t % num_i, jb = t / num_i;
             if (!mbar_wait(smem_u32(&bar->tfull[acc]), acc_phase, abort_flag)) { timed_out = true; break; }
             tc_fence_after();
@@ -360,18 +366,21 @@ absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigne
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// Power-of-two scales: sL = 2^13 (|l| <= 1), sU = 2^(14 - ceil(log2 max|U|));
+// Power-of-two scales: sU = 2^(14 - ceil(log2 max|U|)) and sL = 2^13 when
+// |l| <= 1 (partial pivoting), else sL from max|L| (umax_bits[1]) like sU;
 // writes sL, sU and 1 / (sL sU).
-__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales) {
-    const float umax = __uint_as_float(*umax_bits);
-    int e = 0;
-    if (umax > 0.f && umax < INFINITY) frexpf(umax, &e);  // umax < 2^e
-    const int eu = 14 - e;
-    const float sL = 8192.0f;
-    const float sU = ldexpf(1.0f, eu);
-    scales[0] = sL;
-    scales[1] = sU;
-    scales[2] = ldexpf(1.0f, -13 - eu);
+__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales, int l_from_max) {
+    auto scale_exp = [](unsigned bits) {
+        const float m = __uint_as_float(bits);
+        int e = 0;
+        if (m > 0.f && m < INFINITY) frexpf(m, &e);  // m < 2^e
+        return 14 - e;
+    };
+    const int eu = scale_exp(umax_bits[0]);
+    const int el = l_from_max ? scale_exp(umax_bits[1]) : 13;
+    scales[0] = ldexpf(1.0f, el);
+    scales[1] = ldexpf(1.0f, eu);
+    scales[2] = ldexpf(1.0f, -el - eu);
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -438,9 +447,12 @@ TcWs carve_ws(void *ws, int M, int N, int Kpad, int split) {
     return w;
 }
 
+// nt: U12 is given as its transpose (N x K row-major; C -= L21 U12t^T) and
+// both split scales come from the operands' magnitudes.  lower: only the C
+// tiles on or below the diagonal.
 template <typename H, uint32_t FMT, int SPLIT>
 cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22, long lda,
-                void *ws, MpDevStatus *st, cudaStream_t s) {
+                void *ws, MpDevStatus *st, cudaStream_t s, bool nt = false, int lower = 0) {
     const int Kpad = (K + BK - 1) / BK * BK;
     TcWs w = carve_ws(ws, M, N, Kpad, SPLIT);
     H *Ap = reinterpret_cast<H *>(w.Ap);
@@ -454,18 +466,34 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
         if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(Bp, 0, (size_t)2 * b_lo * Kpad * sizeof(H), s);
         if (e != cudaSuccess) return e;
-        e = cudaMemsetAsync(w.umax, 0, sizeof(unsigned), s);
+        e = cudaMemsetAsync(w.umax, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         const long tot = (long)K * N;
         mp_note_launch();
-        absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(K, N, U12, ldu, w.umax);
+        if (nt)
+            absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(N, K, U12, ldu, w.umax);
+        else
+            absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(K, N, U12, ldu, w.umax);
+        if (nt) {
+            const long totl = (long)M * K;
+            mp_note_launch();
+            absmax_kernel<<<(int)std::min<long>((totl + 255) / 256, 2048L), 256, 0, s>>>(M, K, L21, ldl,
+                                                                                        w.umax + 1);
+        }
         mp_note_launch();
-        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales);
+        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales, nt ? 1 : 0);
     }
     {
-        dim3 grid((N + 31) / 32, (Kpad + 31) / 32);
-        mp_note_launch();
-        pack_transpose_kernel<H, SPLIT><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
+        if (nt) {
+            const long total = (long)N * Kpad;
+            const int blocks = (int)std::min<long>((total + 255) / 256, 4L * 1024);
+            mp_note_launch();
+            pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(N, K, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
+        } else {
+            dim3 grid((N + 31) / 32, (Kpad + 31) / 32);
+            mp_note_launch();
+            pack_transpose_kernel<H, SPLIT><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
+        }
         const long total = (long)M * Kpad;
         const int blocks = (int)std::min<long>((total + 255) / 256, 4L * 1024);
         mp_note_launch();
@@ -486,7 +514,7 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     const int grid = std::min(ntiles, num_sms());
     mp_note_launch();
     kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BK, (int)a_lo, (int)b_lo,
-                                         w.scales + 2, st);
+                                         w.scales + 2, st, lower);
     return cudaGetLastError();
 }
 
@@ -507,5 +535,14 @@ cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, 
     if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_update_nt(int prec, int M, int N, int K, const float *A, long lda, const float *B, long ldb,
+                         float *C, long ldc, int lower, void *ws, MpDevStatus *st, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
+    if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
+    if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
     return cudaErrorInvalidValue;
 }

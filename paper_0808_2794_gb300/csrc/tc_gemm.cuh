@@ -13,6 +13,12 @@ cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, 
                                const float *U12, long ldu, float *A22, long lda, void *ws,
                                MpDevStatus *st, cudaStream_t s);
 
+// C[M x N] -= fl_p(A[M x K]) fl_p(B[N x K])^T (B given row-major N x K, as for
+// the symmetric update A22 -= L21 L21^T); lower != 0: only the tiles of C on
+// or below its diagonal.
+cudaError_t tc_update_nt(int prec, int M, int N, int K, const float *A, long lda, const float *B, long ldb,
+                         float *C, long ldc, int lower, void *ws, MpDevStatus *st, cudaStream_t s);
+
 // Standalone variant for tests/benchmarks: C[M x N] -= A[M x K] B[K x N].
 cudaError_t tc_gemm_sub(int prec, int M, int N, int K, const float *A, long lda, const float *B,
                         long ldb, float *C, long ldc, void *ws, size_t ws_bytes, MpDevStatus *st,

@@ -40,7 +40,8 @@ template <typename T> constexpr int base_bs() { return sizeof(T) == 4 ? 128 : 64
 // ---- inverses of the base diagonal blocks, written into the BI x BI layout
 template <typename T, int BS>
 __global__ void __launch_bounds__(BS)
-base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restrict__ Linv, T *__restrict__ Uinv) {
+base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restrict__ Linv, T *__restrict__ Uinv,
+                    int lower_unit, int upper_unit) {
     extern __shared__ __align__(16) unsigned char raw[];
     T(*blk)[BS + 1] = reinterpret_cast<T(*)[BS + 1]>(raw);
     T(*x)[BS + 1] = reinterpret_cast<T(*)[BS + 1]>(raw + sizeof(T) * BS * (BS + 1));
@@ -54,19 +55,20 @@ base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restr
         blk[i][c] = in ? W[(long)(r0 + i) * ldw + r0 + c] : T(i == c ? 1 : 0);
     }
     __syncthreads();
-    // unit lower: x_i = delta_ic - sum_{l<i} L_il x_l (thread c owns column c)
+    // lower: x_i = (delta_ic - sum_{l<i} L_il x_l) / L_ii, L_ii = 1 when unit
+    // (thread c owns column c)
     for (int i = 0; i < BS; ++i) {
         T s = T(i == c ? 1 : 0);
         for (int l = c; l < i; ++l) s = fma(-blk[i][l], x[l][c], s);
-        x[i][c] = (i < c) ? T(0) : s;
+        x[i][c] = (i < c) ? T(0) : (lower_unit ? s : s / blk[i][i]);
     }
     for (int i = 0; i < bs; ++i)
         if (c < bs) Linv[dst + (long)i * BI + c] = x[i][c];
-    // upper: x_i = (delta_ic - sum_{l>i} U_il x_l) / U_ii
+    // upper: x_i = (delta_ic - sum_{l>i} U_il x_l) / U_ii, U_ii = 1 when unit
     for (int i = BS - 1; i >= 0; --i) {
         T s = T(i == c ? 1 : 0);
         for (int l = i + 1; l <= c; ++l) s = fma(-blk[i][l], x[l][c], s);
-        x[i][c] = (i > c) ? T(0) : s / blk[i][i];
+        x[i][c] = (i > c) ? T(0) : (upper_unit ? s : s / blk[i][i]);
     }
     for (int i = 0; i < bs; ++i)
         if (c < bs) Uinv[dst + (long)i * BI + c] = x[i][c];
@@ -179,7 +181,7 @@ trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ld
         T v;
         if (LOWER) {
             const double s = pow2_ceil(rnorm[h]);
-            v = (T)(R[(long)h * ldr + perm[r]] / s);
+            v = (T)(R[(long)h * ldr + (perm ? perm[r] : r)] / s);
         } else {
             v = Yin[(long)h * ldyin + r];
         }
@@ -297,7 +299,8 @@ template size_t trsv_tmp_bytes<double>(int);
 // Builds inv(L_bb) and inv(U_bb) for the BI x BI diagonal blocks of the
 // row-major factors in W.  tmp holds trsv_tmp_bytes<T>(n).
 template <typename T>
-cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s) {
+cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
+                                  bool lower_unit, bool upper_unit) {
     if (n <= 0) return cudaSuccess;
     constexpr int BS = base_bs<T>();
     const int BI = trsv_inverse_block<T>(n);
@@ -313,7 +316,7 @@ cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv,
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         mp_note_launch();
-        kern<<<(n + BS - 1) / BS, BS, smem, s>>>(n, BI, W, ldw, Linv, Uinv);
+        kern<<<(n + BS - 1) / BS, BS, smem, s>>>(n, BI, W, ldw, Linv, Uinv, lower_unit ? 1 : 0, upper_unit ? 1 : 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -369,9 +372,10 @@ cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv,
     }
     return cudaSuccess;
 }
-template cudaError_t launch_build_inverses<float>(int, const float *, long, float *, float *, float *, cudaStream_t);
+template cudaError_t launch_build_inverses<float>(int, const float *, long, float *, float *, float *, cudaStream_t,
+                                                  bool, bool);
 template cudaError_t launch_build_inverses<double>(int, const double *, long, double *, double *, double *,
-                                                   cudaStream_t);
+                                                   cudaStream_t, bool, bool);
 
 template <typename T>
 cudaError_t launch_trsv_lower(int n, int nrhs, const T *W, long ldw, const T *Linv, const double *R, long ldr,

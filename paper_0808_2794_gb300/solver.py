@@ -65,10 +65,18 @@ _SIGS = {
     "mp_gesv_host_workspace_bytes": (_Z, [_I, _I, ctypes.POINTER(mp_opts)]),
     "mp_gesv_host": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _P, _Z, ctypes.POINTER(mp_opts),
                           ctypes.POINTER(mp_stats), _P]),
+    "mp_posv_workspace_bytes": (_Z, [_I, _I, ctypes.POINTER(mp_opts)]),
+    "mp_posv": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _Z, ctypes.POINTER(mp_opts),
+                     ctypes.POINTER(mp_stats), _P]),
+    "mp_gesv_adjoint_workspace_bytes": (_Z, [_I, ctypes.POINTER(mp_opts)]),
+    "mp_gesv_adjoint": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _Z, _P, _Z,
+                             ctypes.POINTER(mp_opts), ctypes.POINTER(mp_stats), _P]),
     "mp_factor_ld": (_I, [_I]),
     "mp_getrf_workspace_bytes": (_Z, [_I, ctypes.POINTER(mp_opts)]),
     "mp_convert": (_I, [_I, _P, _I, _P, _I, _P, _P, _P, _Z, _P]),
     "mp_getrf_lowp": (_I, [_I, _P, _I, _P, ctypes.POINTER(mp_opts), _P, _Z,
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32), _P]),
+    "mp_potrf_lowp": (_I, [_I, _P, _I, ctypes.POINTER(mp_opts), _P, _Z,
                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32), _P]),
     "mp_getrs_workspace_bytes": (_Z, [_I, _I]),
     "mp_getrs_lowp": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _I, _P, _Z, _P]),
@@ -194,7 +202,7 @@ def workspace(nbytes: int, device=None):
 
 
 def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
-         nb_outer=0, work=None, stream=None):
+         nb_outer=0, gmres_restart=30, gmres_tol=1e-6, work=None, stream=None):
     """Solve A X = B (Algorithm 1).  A: (n, n) float64 CUDA tensor, B: (n,) or
     (n, nrhs).  Returns (X, ipiv, stats) with X column-major float64 and ipiv
     int32 (LAPACK 1-based)."""
@@ -205,7 +213,8 @@ def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fal
     B = colmajor(B)
     n, nrhs = B.shape
     opts = default_opts(prec=prec, refine=refine, itermax=itermax, tol=tol,
-                        allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer)
+                        allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer,
+                        gmres_restart=gmres_restart, gmres_tol=gmres_tol)
     X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
     ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     need = lib.mp_gesv_workspace_bytes(n, nrhs, ctypes.byref(opts))
@@ -221,8 +230,103 @@ def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fal
     return (X[:, 0] if squeeze else X), ipiv[:n], d
 
 
-def gesv_host(A, B, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True, nb_outer=0,
-              work=None, stream=None):
+def posv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
+         nb_outer=0, gmres_restart=30, gmres_tol=1e-6, work=None, stream=None):
+    """Solve A X = B for symmetric positive definite A from its lower triangle
+    (Cholesky variant).  Returns (X, stats); stats["info_fp64"] > 0 when A is
+    not positive definite."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = B.dim() == 1
+    B = colmajor(B)
+    n, nrhs = B.shape
+    opts = default_opts(prec=prec, refine=refine, itermax=itermax, tol=tol,
+                        allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer,
+                        gmres_restart=gmres_restart, gmres_tol=gmres_tol)
+    X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    need = lib.mp_posv_workspace_bytes(n, nrhs, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    st = mp_stats()
+    ret = lib.mp_posv(n, nrhs, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(), _ld(X),
+                      work.data_ptr(), work.numel(), ctypes.byref(opts), ctypes.byref(st),
+                      _stream_ptr(stream))
+    _check(ret, "mp_posv")
+    d = st.as_dict()
+    d["info_fp64"] = ret
+    return (X[:, 0] if squeeze else X), d
+
+
+def gesv_adjoint(A, X, G, work, prec="fp32", allow_fallback=True, nb_outer=0, adj_work=None,
+                 stream=None):
+    """Bbar = A^{-T} G and Abar = -Bbar X^T from the factors a preceding gesv /
+    posv call left in `work` (pass that call's workspace and options).
+    Returns (Abar, Bbar, stats)."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = G.dim() == 1
+    G = colmajor(G)
+    X = colmajor(X)
+    n, nrhs = G.shape
+    opts = default_opts(prec=prec, allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer)
+    need = lib.mp_gesv_adjoint_workspace_bytes(n, ctypes.byref(opts))
+    if adj_work is None or adj_work.numel() < need:
+        adj_work = workspace(need, A.device)
+    Bbar = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    Abar = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    st = mp_stats()
+    ret = lib.mp_gesv_adjoint(n, nrhs, A.data_ptr(), _ld(A), X.data_ptr(), _ld(X), G.data_ptr(), _ld(G),
+                              Bbar.data_ptr(), _ld(Bbar), Abar.data_ptr(), max(n, 1),
+                              work.data_ptr(), work.numel(), adj_work.data_ptr(), adj_work.numel(),
+                              ctypes.byref(opts), ctypes.byref(st), _stream_ptr(stream))
+    _check(ret, "mp_gesv_adjoint")
+    return Abar, (Bbar[:, 0] if squeeze else Bbar), st.as_dict()
+
+
+def _make_solve_fn():
+    torch = _torch()
+
+    class SolveFn(torch.autograd.Function):
+        """X = A^{-1} B with mixed-precision refinement; backward through the
+        adjoint solve with the same factors (Abar = -A^{-T} G X^T,
+        Bbar = A^{-T} G)."""
+
+        @staticmethod
+        def forward(ctx, A, B, prec="fp32", nb_outer=0):
+            work = workspace(load().mp_gesv_workspace_bytes(
+                A.shape[0], 1 if B.dim() == 1 else B.shape[1],
+                ctypes.byref(default_opts(prec=prec, nb_outer=nb_outer))), A.device)
+            X, _, st = gesv(A.detach(), B.detach(), prec=prec, nb_outer=nb_outer, work=work)
+            X = X.contiguous() if X.dim() == 1 else X
+            ctx.save_for_backward(A, X)
+            ctx.work, ctx.prec, ctx.nb_outer, ctx.vec = work, prec, nb_outer, B.dim() == 1
+            return X.clone()
+
+        @staticmethod
+        def backward(ctx, G):
+            A, X = ctx.saved_tensors
+            Abar, Bbar, _ = gesv_adjoint(A.detach(), X, G.contiguous(), ctx.work, prec=ctx.prec,
+                                         nb_outer=ctx.nb_outer)
+            return Abar, Bbar, None, None
+
+    return SolveFn
+
+
+def solve_fn():
+    """The torch.autograd.Function of the solve (built on first use)."""
+    global _SOLVE_FN
+    if _SOLVE_FN is None:
+        _SOLVE_FN = _make_solve_fn()
+    return _SOLVE_FN
+
+
+_SOLVE_FN = None
+
+
+def gesv_host(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
+              nb_outer=0, work=None, stream=None):
     """Same as gesv with host (numpy, column-major float64) A and B; the host to
     device copies happen inside the C call."""
     import numpy as np
@@ -233,7 +337,7 @@ def gesv_host(A, B, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True, nb_
     n, nrhs = B.shape
     X = np.zeros((n, nrhs), dtype=np.float64, order="F")
     ipiv = np.zeros(max(n, 1), dtype=np.int32)
-    opts = default_opts(prec=prec, itermax=itermax, tol=tol,
+    opts = default_opts(prec=prec, refine=refine, itermax=itermax, tol=tol,
                         allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer)
     need = lib.mp_gesv_host_workspace_bytes(n, nrhs, ctypes.byref(opts))
     if work is None or work.numel() < need:
@@ -286,6 +390,23 @@ def getrf_lowp(W, prec="fp32", nb_outer=0, work=None, stream=None):
                              work.data_ptr(), work.numel(), ctypes.byref(info), ctypes.byref(flags),
                              _stream_ptr(stream)), "mp_getrf_lowp")
     return ipiv[:n], info.value, flags.value
+
+
+def potrf_lowp(W, prec="fp32", nb_outer=0, work=None, stream=None):
+    """In-place Cholesky (lower) of the row-major FP32 W (n x ldw).
+    Returns (info, flags)."""
+    lib = load()
+    n, ldw = W.shape
+    opts = default_opts(prec=prec, nb_outer=nb_outer)
+    need = lib.mp_getrf_workspace_bytes(n, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need, W.device)
+    info = ctypes.c_int(0)
+    flags = ctypes.c_uint32(0)
+    _check(lib.mp_potrf_lowp(n, W.data_ptr(), ldw, ctypes.byref(opts), work.data_ptr(), work.numel(),
+                             ctypes.byref(info), ctypes.byref(flags), _stream_ptr(stream)),
+           "mp_potrf_lowp")
+    return info.value, flags.value
 
 
 def getrs_lowp(W, ipiv, R, work=None, stream=None):
