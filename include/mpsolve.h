@@ -147,6 +147,27 @@ MP_API int mp_posv(int n, int nrhs, const double *dA, int lda, const double *dB,
                    int ldx, void *work, size_t work_bytes, const mp_opts *opts, mp_stats *stats,
                    void *stream);
 
+/* Batched solve of many independent small systems A_i X_i = B_i (Algorithm 1
+ * per system; Section 2.1's payoff discussion: small problems are where the
+ * low-precision factorization pays least, so each system runs entirely on one
+ * SM inside a single persistent launch).  n[i] in [0, MP_BATCH_MAX_N],
+ * nrhs[i] in [0, 8]; n, nrhs, lda, ldb, ldx, iter, flags, info are HOST
+ * arrays of `batch` entries; A, B, X, ipiv are HOST arrays of DEVICE
+ * pointers (column-major FP64 A_i, B_i, X_i; int32 ipiv_i, LAPACK 1-based).
+ * opts->prec in {FP32, BF16, FP16} (trailing-update operands rounded to p,
+ * FP32 products and sums on the CUDA cores).  Per system: iter[i] =
+ * corrections applied or -1 when the FP64 fallback answered, flags[i] =
+ * MP_FLAG_*, info[i] = first zero pivot of the FP64 factorization (> 0:
+ * singular) or 0; iter, flags and info may be NULL.  The call returns after
+ * the results are on the host.  Returns 0 or -i for an illegal argument i
+ * (1..17 in order). */
+#define MP_BATCH_MAX_N 512
+MP_API size_t mp_gesv_batched_workspace_bytes(int batch, const int *n, const int *nrhs, const mp_opts *opts);
+MP_API int mp_gesv_batched(int batch, const int *n, const int *nrhs, const double *const *A, const int *lda,
+                           const double *const *B, const int *ldb, double *const *X, const int *ldx,
+                           int32_t *const *ipiv, int *iter, unsigned *flags, int *info, void *work,
+                           size_t work_bytes, const mp_opts *opts, void *stream);
+
 /* Adjoint of the solve (reverse-mode derivative of X = A^{-1} B; the paper
  * has no counterpart).  Given the FP64 cotangent G = dL/dX (n x nrhs),
  * computes Bbar = A^{-T} G (n x nrhs) and Abar = -Bbar X^T (n x n, FP64,
