@@ -4,8 +4,11 @@
 Workload (default): dense nonsymmetric system, n = 16384, nrhs = 1, A i.i.d.
 N(0,1), x_true i.i.d. U[-1,1], b = A x_true in FP64 (seeded, synthetic).  One
 step = one whole mixed-precision solve through the C ABI (mp_gesv): FP64->FP32
-conversion, low-precision LU with partial pivoting, FP64 iterative refinement
-to a normwise backward error <= 1e-14 (and the FP64 fallback, if taken).
+conversion, low-precision LU with partial pivoting (default rung fp16x3: the
+trailing updates as three fp16 tensor-core products, about FP32 accurate),
+FP64 iterative refinement to a normwise backward error <= 1e-14 (and the FP64
+fallback, if taken).  --workload chol|batched|adjoint times the secondary
+workloads instead (one JSON line each, not the headline).
 
   value      = (2 n^3 / 3) * N_ranks / (max-over-ranks time per step), GFLOP/s,
                inputs resident in HBM (A is 2.1 GB, larger than L2).
@@ -159,6 +162,80 @@ def run_reference(args):
 METRIC = "FP64-accurate solve GFLOP/s (2n^3/3) at bwd err <= 1e-14 vs plain FP64 LU, 1 GB300"
 
 
+def run_secondary(args):
+    """Times one of the secondary workloads on one GPU (not the headline
+    line): SPD Cholesky solve (n=4096, nrhs=4, prescribed kappa), the batch of
+    4096 small systems, or the adjoint solve (n=2048, nrhs=8).  Prints one
+    JSON line with the workload's own metric."""
+    import ctypes
+    import torch
+    from paper_0808_2794_gb300 import inputs, solver
+    torch.cuda.set_device(0)
+    lib = solver.load()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    extra = {}
+    if args.workload == "chol":
+        n, nrhs = (args.n if args.n != 16384 else 4096), 4
+        A, B, _ = inputs.conditioned_system(n, args.kappa, nrhs=nrhs, spd=True, seed=0)
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        o = solver.default_opts(prec=args.prec, refine=args.refine)
+        work = solver.workspace(lib.mp_posv_workspace_bytes(n, nrhs, ctypes.byref(o)))
+        step = lambda: solver.posv(Ad, Bd, prec=args.prec, refine=args.refine, work=work)[1]
+        flops = n ** 3 / 3.0
+        metric = "FP64-accurate SPD solve GFLOP/s (n^3/3) at bwd err <= 1e-14, 1 GB300"
+        cfg = {"workload": f"SPD Cholesky solve, A = U diag(s) U^T, kappa={args.kappa:g}, n={n}, nrhs={nrhs}"}
+    elif args.workload == "batched":
+        As, Bs, _ = inputs.batched_systems(count=4096, seed=0)
+        dA = [torch.from_numpy(a).cuda() for a in As]
+        dB = [torch.from_numpy(b).cuda() for b in Bs]
+        prec = args.prec if args.prec in ("fp32", "bf16", "fp16") else "fp32"
+        flops = sum(2.0 * a.shape[0] ** 3 / 3.0 for a in As)
+        plan = solver.BatchedPlan(dA, dB, prec=prec)  # argument tables built once, outside the timing
+
+        def step():
+            plan.run()
+            it, fl = plan.iter, plan.flags
+            return {"iter_max": int(it.max()), "flags_or": int(np.bitwise_or.reduce(fl)),
+                    "n_fallback": int(np.sum(it < 0))}
+        metric = "batched FP64-accurate solve GFLOP/s (sum 2n^3/3), 1 GB300"
+        cfg = {"workload": "4096 systems, n log-uniform [16,512], nrhs 1..4, A = N(0,1) + n I",
+               "prec": prec}
+    else:  # adjoint
+        n, nrhs = (args.n if args.n != 16384 else 2048), 8
+        A, B, Wt = inputs.adjoint_problem(n, nrhs, seed=0)
+        Ad, Bd, Gd = (torch.from_numpy(x).cuda() for x in (A, B, Wt))
+        o = solver.default_opts(prec=args.prec)
+        work = solver.workspace(lib.mp_gesv_workspace_bytes(n, nrhs, ctypes.byref(o)))
+        adj = solver.workspace(lib.mp_gesv_adjoint_workspace_bytes(n, ctypes.byref(o)))
+        X, _, _ = solver.gesv(Ad, Bd, prec=args.prec, work=work)
+
+        def step():
+            return solver.gesv_adjoint(Ad, X, Gd, work, prec=args.prec, adj_work=adj)[2]
+        flops = 8.0 * n * n  # reported as GB/s of the n x n FP64 Abar write
+        metric = "adjoint solve (Bbar = A^-T G, Abar = -Bbar X^T) Abar write GB/s"
+        cfg = {"workload": f"adjoint of X = A^-1 B, A = N(0,1) + sqrt(n) I, n={n}, nrhs={nrhs}"}
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = solver.launch_count()
+    ev[0].record(stream)
+    out = None
+    for _ in range(args.steps):
+        out = step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    value = flops / (ms * 1e-3) / 1e9
+    line = {"metric": metric, "value": value, "unit": "GFLOP/s" if args.workload != "adjoint" else "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": f"{args.prec}-factor/f64-refine", "data": "synthetic",
+            "config": cfg, "gpu_launches": solver.launch_count() - launches0,
+            "solve": {k: v for k, v in (out or {}).items() if not isinstance(v, list)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,7 +244,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--prec", default="fp16x3")
+    ap.add_argument("--refine", default="classical", choices=["classical", "gmres", "auto"])
+    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint"],
+                    help="lu: the headline dense solve; the others time the secondary "
+                         "workloads (SPD Cholesky, batched small systems, adjoint solve)")
+    ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--ref-n", type=int, default=2048)
     ap.add_argument("--cpu-n", type=int, default=3072)
@@ -176,6 +258,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "lu":
+        return run_secondary(args)
 
     import torch
     from paper_0808_2794_gb300 import inputs, solver
@@ -196,7 +280,7 @@ def main():
     A, B, Xtrue = inputs.dense_system(n, nrhs=nrhs, seed=rank)
     Ad = torch.from_numpy(np.asfortranarray(A)).cuda()
     Bd = torch.from_numpy(np.asfortranarray(B)).cuda()
-    opts = dict(prec=args.prec, nb_outer=args.nb)
+    opts = dict(prec=args.prec, nb_outer=args.nb, refine=args.refine)
     lib = solver.load()
     import ctypes
     o = solver.default_opts(**opts)
@@ -259,7 +343,7 @@ def main():
     peaks = load_peaks()
     ms_d, nl_d, work_d = prof[dom]
     if dom in ("update", "trsm", "panelgemm", "panel"):
-        tensor = dom == "update" and args.prec in ("bf16", "fp16")
+        tensor = dom == "update" and args.prec in ("bf16", "fp16", "fp16x3")
         if tensor:
             bound, unit, peak = "tensor", "TFLOP/s", peaks.get("bf16_tflops_sustained", 1700.0)
         else:

@@ -43,14 +43,6 @@ template <typename T> struct BCfg;
 template <> struct BCfg<float> { static constexpr int NB = 32; };
 template <> struct BCfg<double> { static constexpr int NB = 16; };
 
-template <typename T>
-constexpr size_t batched_smem_bytes() {
-    constexpr int NB = BCfg<T>::NB;
-    return sizeof(T) * (size_t)kMaxN * (NB + 1)       // panel
-           + sizeof(T) * (size_t)NB * kMaxN           // U12 block / vectors
-           + sizeof(double) * (size_t)kMaxN * kMaxRhs // x (FP64) for the residual
-           + 1024;                                    // reductions and scalars
-}
 
 __device__ __forceinline__ double pow2_ceil_d(double v) {
     if (!(v > 0.0) || !(v <= 1.79769313486231570815e308)) return 1.0;
@@ -76,7 +68,23 @@ struct Shared {
     double bnorm[kMaxRhs], rnorm[kMaxRhs], xnorm[kMaxRhs], znorm[kMaxRhs], zprev[kMaxRhs];
     int piv, sys, stop, info;
     unsigned flags;
+    int nmoves;
+    int rowsrc[64], mdst[64], pv[64];  // composed row moves of one panel (<= 2 NB)
 };
+
+// Dynamic shared memory: panel, U12 block (also the solve vectors), x in
+// FP64 for the residual, then the Shared block (8-byte aligned after the
+// double array).
+template <typename T>
+constexpr size_t batched_smem_bytes() {
+    constexpr int NB = BCfg<T>::NB;
+    return sizeof(T) * (size_t)kMaxN * (NB + 1)       // panel
+           + sizeof(T) * (size_t)NB * kMaxN           // U12 block / vectors
+           + sizeof(double) * (size_t)kMaxN * kMaxRhs // x (FP64) for the residual
+           + sizeof(Shared);                          // reductions, scalars, row moves
+}
+static_assert((sizeof(float) * (size_t)kMaxN * 33 + sizeof(float) * 32 * kMaxN) % 8 == 0, "alignment");
+static_assert((sizeof(double) * (size_t)kMaxN * 17 + sizeof(double) * 16 * kMaxN) % 8 == 0, "alignment");
 
 // Block-wide max of a non-negative double (NaN counts as +inf).
 __device__ double block_max(double v, Shared &sh) {
@@ -146,37 +154,57 @@ __device__ void lu_factor(const BatchSys &d, T *W, int ldw, T *P, T *Us, Shared 
             if (ok)
                 for (int r = j + 1 + tid; r < m; r += NT) P[r * (NB + 1) + j] = P[r * (NB + 1) + j] / dg;
             __syncthreads();
-            if (ok) {
-                const int w = nb - j - 1;
-                for (int e = tid; e < (m - j - 1) * w; e += NT) {
-                    const int r = j + 1 + e / w, c = j + 1 + e % w;
-                    P[r * (NB + 1) + c] = fma(-P[r * (NB + 1) + j], P[j * (NB + 1) + c], P[r * (NB + 1) + c]);
+            if (ok)
+                for (int r = j + 1 + tid; r < m; r += NT) {
+                    T *pr = P + r * (NB + 1);
+                    const T lr = pr[j];
+                    for (int c = j + 1; c < nb; ++c) pr[c] = fma(-lr, P[j * (NB + 1) + c], pr[c]);
                 }
-            }
             __syncthreads();
         }
         for (int e = tid; e < m * nb; e += NT) {
             const int r = e / nb, c = e - r * nb;
             W[(long)(k + r) * ldw + k + c] = P[r * (NB + 1) + c];
         }
-        // the panel's interchanges on the columns outside it, in order
-        for (int j = 0; j < nb; ++j) {
-            const int p = d.ipiv[k + j] - 1;
-            if (p != k + j) {
-                for (int c = tid; c < n; c += NT) {
-                    if (c >= k && c < k + nb) continue;
-                    const T t = W[(long)(k + j) * ldw + c];
-                    W[(long)(k + j) * ldw + c] = W[(long)p * ldw + c];
-                    W[(long)p * ldw + c] = t;
+        // the panel's interchanges on the columns outside it: composed into at
+        // most 2 nb (destination, source) row moves, then every thread moves
+        // whole columns with all loads in flight before the stores
+        if (tid == 0) {
+            int *src = sh.rowsrc;  // rows k.. : which original row is now there
+            int nmv = 0;
+            for (int j = 0; j < nb; ++j) {
+                const int p = d.ipiv[k + j] - 1 - k;
+                // rows are looked up by position; untouched rows hold themselves
+                int a = -1, b = -1;
+                for (int t = 0; t < nmv; ++t) {
+                    if (sh.mdst[t] == j) a = t;
+                    if (sh.mdst[t] == p) b = t;
                 }
-                if (tid == 0) {
-                    const int t = d.perm[k + j];
-                    d.perm[k + j] = d.perm[p];
-                    d.perm[p] = t;
-                }
+                if (p == j) continue;
+                if (a < 0) { sh.mdst[nmv] = j; src[nmv] = j; a = nmv++; }
+                if (b < 0) { sh.mdst[nmv] = p; src[nmv] = p; b = nmv++; }
+                const int t = src[a];
+                src[a] = src[b];
+                src[b] = t;
             }
-            __syncthreads();
+            sh.nmoves = nmv;
         }
+        __syncthreads();
+        const int nmv = sh.nmoves;
+        for (int c = tid; c < n; c += NT) {
+            if (c >= k && c < k + nb) continue;
+            T v[2 * NB];
+#pragma unroll
+            for (int t = 0; t < 2 * NB; ++t)
+                if (t < nmv) v[t] = W[(long)(k + sh.rowsrc[t]) * ldw + c];
+#pragma unroll
+            for (int t = 0; t < 2 * NB; ++t)
+                if (t < nmv) W[(long)(k + sh.mdst[t]) * ldw + c] = v[t];
+        }
+        if (tid < nmv) sh.pv[tid] = d.perm[k + sh.rowsrc[tid]];
+        __syncthreads();
+        if (tid < nmv) d.perm[k + sh.mdst[tid]] = sh.pv[tid];
+        __syncthreads();
         const int rest = n - k - nb;
         if (rest <= 0) continue;
         // U12 = L11^{-1} A12 (unit lower L11 from the panel), one column per thread
@@ -209,9 +237,14 @@ __device__ void lu_factor(const BatchSys &d, T *W, int ldw, T *P, T *Us, Shared 
             for (int c0 = 0; c0 < rest; c0 += 64) {
                 T acc[4][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a) {
+                    const int r = r0 + ty * 4 + a;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = c0 + tx * 4 + b;
+                        acc[a][b] = (r < rest && c < rest) ? W[(long)(k + nb + r) * ldw + k + nb + c] : T(0);
+                    }
+                }
                 for (int l = 0; l < nb; ++l) {
                     T av[4], bv[4];
 #pragma unroll
@@ -227,7 +260,7 @@ __device__ void lu_factor(const BatchSys &d, T *W, int ldw, T *P, T *Us, Shared 
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -237,7 +270,7 @@ __device__ void lu_factor(const BatchSys &d, T *W, int ldw, T *P, T *Us, Shared 
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int c = c0 + tx * 4 + b;
-                        if (c < rest) row[c] -= acc[a][b];
+                        if (c < rest) row[c] = acc[a][b];
                     }
                 }
             }
@@ -245,55 +278,79 @@ __device__ void lu_factor(const BatchSys &d, T *W, int ldw, T *P, T *Us, Shared 
     }
 }
 
-// v[c][i] (shared, T) <- U^{-1} L^{-1} v, unit L / non-unit U from W; 32-row
-// blocks: warp 0 solves the diagonal block (lane = row), then every thread
-// updates the rows after (before) it.
+// Inverses of the 32 x 32 diagonal blocks of L (unit lower) and U (upper)
+// into Dinv (block b: L^{-1} at Dinv + 2048 b, U^{-1} at Dinv + 2048 b + 1024,
+// row-major 32 x 32).  One warp per block, lane = column of the inverse;
+// the block is staged in shared memory (buf: 8 x 32 x 33 T).
 template <typename T>
-__device__ void lu_solve(int n, int nrhs, const T *W, int ldw, T *v) {
-    const int tid = threadIdx.x, lane = tid & 31;
+__device__ void diag_inverses(int n, const T *W, int ldw, T *Dinv, T *buf) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nbk = (n + 31) / 32;
-    for (int b = 0; b < nbk; ++b) {  // forward, unit lower
+    T(*blk)[33] = reinterpret_cast<T(*)[33]>(buf + warp * 32 * 33);
+    for (int b = warp; b < nbk; b += NT / 32) {
         const int r0 = b * 32, bs = min(32, n - r0);
-        if (tid < 32)
-            for (int c = 0; c < nrhs; ++c) {
-                T x = lane < bs ? v[c * kMaxN + r0 + lane] : T(0);
-                for (int j = 0; j < bs; ++j) {
-                    const T xj = __shfl_sync(0xffffffffu, x, j);
-                    if (lane > j && lane < bs) x = fma(-W[(long)(r0 + lane) * ldw + r0 + j], xj, x);
-                }
-                if (lane < bs) v[c * kMaxN + r0 + lane] = x;
-            }
-        __syncthreads();
-        for (int e = tid; e < (n - r0 - bs) * nrhs; e += NT) {
-            const int c = e / (n - r0 - bs), i = r0 + bs + e % (n - r0 - bs);
-            const T *wr = W + (long)i * ldw + r0;
-            T s = v[c * kMaxN + i];
-            for (int j = 0; j < bs; ++j) s = fma(-wr[j], v[c * kMaxN + r0 + j], s);
-            v[c * kMaxN + i] = s;
+        for (int i = 0; i < 32; ++i) blk[i][lane] = (i < bs && lane < bs) ? W[(long)(r0 + i) * ldw + r0 + lane] : T(i == lane ? 1 : 0);
+        __syncwarp();
+        T x[32];
+        // unit lower: x_i = delta_ic - sum_{l<i} L_il x_l (c = lane)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            T s = T(i == lane ? 1 : 0);
+#pragma unroll
+            for (int l = 0; l < i; ++l) s = fma(-blk[i][l], x[l], s);
+            x[i] = s;
         }
-        __syncthreads();
+        T *Li = Dinv + (long)b * 2048;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Li[i * 32 + lane] = x[i];
+        // upper: x_i = (delta_ic - sum_{l>i} U_il x_l) / U_ii
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            T s = T(i == lane ? 1 : 0);
+#pragma unroll
+            for (int l = i + 1; l < 32; ++l) s = fma(-blk[i][l], x[l], s);
+            x[i] = s / blk[i][i];
+        }
+        T *Ui = Li + 1024;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Ui[i * 32 + lane] = x[i];
+        __syncwarp();
     }
-    for (int b = nbk - 1; b >= 0; --b) {  // backward, non-unit upper
-        const int r0 = b * 32, bs = min(32, n - r0);
-        if (tid < 32)
-            for (int c = 0; c < nrhs; ++c) {
-                T x = lane < bs ? v[c * kMaxN + r0 + lane] : T(0);
-                for (int j = bs - 1; j >= 0; --j) {
-                    if (lane == j) x = x / W[(long)(r0 + j) * ldw + r0 + j];
-                    const T xj = __shfl_sync(0xffffffffu, x, j);
-                    if (lane < j) x = fma(-W[(long)(r0 + lane) * ldw + r0 + j], xj, x);
-                }
-                if (lane < bs) v[c * kMaxN + r0 + lane] = x;
+}
+
+// v[c][i] (shared, T) <- U^{-1} L^{-1} v with the factors in W and the
+// diagonal-block inverses in Dinv: per 32-row block, y_b = D_b^{-1} v_b
+// (thread = (row, rhs)), then the rows after (before) it are updated with
+// the block's columns (thread = (row, rhs), 128-byte row segments of W).
+template <typename T>
+__device__ void lu_solve(int n, int nrhs, const T *W, int ldw, const T *Dinv, T *v, T *tmp) {
+    const int tid = threadIdx.x;
+    const int nbk = (n + 31) / 32;
+    const int r = tid & 31, c = tid >> 5;  // 8 right-hand sides at most
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < nbk; ++q) {
+            const int b = pass == 0 ? q : nbk - 1 - q;
+            const int r0 = b * 32, bs = min(32, n - r0);
+            const T *D = Dinv + (long)b * 2048 + (pass == 0 ? 0 : 1024);
+            if (c < nrhs && r < bs) {
+                const T *drow = D + r * 32;
+                T s = T(0);
+                for (int k = 0; k < bs; ++k) s = fma(drow[k], v[c * kMaxN + r0 + k], s);
+                tmp[c * 32 + r] = s;
             }
-        __syncthreads();
-        for (int e = tid; e < r0 * nrhs; e += NT) {
-            const int c = e / r0, i = e % r0;
-            const T *wr = W + (long)i * ldw + r0;
-            T s = v[c * kMaxN + i];
-            for (int j = 0; j < bs; ++j) s = fma(-wr[j], v[c * kMaxN + r0 + j], s);
-            v[c * kMaxN + i] = s;
+            __syncthreads();
+            if (c < nrhs && r < bs) v[c * kMaxN + r0 + r] = tmp[c * 32 + r];
+            __syncthreads();
+            const int lo = pass == 0 ? r0 + bs : 0, hi = pass == 0 ? n : r0;
+            for (int e = tid; e < (hi - lo) * nrhs; e += NT) {
+                const int cc = e / (hi - lo), i = lo + e % (hi - lo);
+                const T *wr = W + (long)i * ldw + r0;
+                T s = v[cc * kMaxN + i];
+                for (int j = 0; j < bs; ++j) s = fma(-wr[j], v[cc * kMaxN + r0 + j], s);
+                v[cc * kMaxN + i] = s;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -327,8 +384,18 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
         double rmax = 0.0;
         bool bad = false;
         for (int i = tid; i < n; i += NT) {
+            // 16 loads in flight per thread, summed in column order
             double s = 0.0;
-            for (int j = 0; j < n; ++j) s += fabs(d.A[(long)j * d.lda + i]);
+            const double *ai = d.A + i;
+            int j = 0;
+            for (; j + 16 <= n; j += 16) {
+                double a[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) a[t] = __ldcs(ai + (long)(j + t) * d.lda);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) s += fabs(a[t]);
+            }
+            for (; j < n; ++j) s += fabs(ai[(long)j * d.lda]);
             if (!(s <= 1.79769313486231570815e308)) bad = true;
             rmax = fmax(rmax, s);
         }
@@ -371,14 +438,19 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
             __syncthreads();
             continue;
         }
+        // ---- diagonal-block inverses for the solves (panel buffer as scratch)
+        T *Dinv = static_cast<T *>(d.Dinv);
+        diag_inverses<T>(n, W, ldw, Dinv, P);
+        __syncthreads();
         // ---- x0 = M b, then the refinement loop (steps 4-7)
         T *v = Us;  // nrhs x kMaxN vectors
+        T *tmp = P;  // 8 x 32 scratch of the solves
         for (int e = tid; e < n * nrhs; e += NT) {
             const int c = e / n, i = e % n;
             v[c * kMaxN + i] = (T)(d.B[(long)c * d.ldb + d.perm[i]] / pow2_ceil_d(sh.bnorm[c]));
         }
         __syncthreads();
-        lu_solve<T>(n, nrhs, W, ldw, v);
+        lu_solve<T>(n, nrhs, W, ldw, Dinv, v, tmp);
         for (int e = tid; e < n * nrhs; e += NT) {
             const int c = e / n, i = e % n;
             const double z = (double)v[c * kMaxN + i] * pow2_ceil_d(sh.bnorm[c]);
@@ -403,8 +475,20 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
                 double acc[kMaxRhs];
 #pragma unroll
                 for (int c = 0; c < kMaxRhs; ++c) acc[c] = 0.0;
-                for (int j = 0; j < n; ++j) {
-                    const double a = d.A[(long)j * d.lda + i];
+                const double *ai = d.A + i;
+                int j = 0;
+                for (; j + 16 <= n; j += 16) {  // 16 loads in flight, products in column order
+                    double a[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) a[t] = ai[(long)(j + t) * d.lda];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t)
+#pragma unroll
+                        for (int c = 0; c < kMaxRhs; ++c)
+                            if (c < nrhs) acc[c] = fma(a[t], xs[c * kMaxN + j + t], acc[c]);
+                }
+                for (; j < n; ++j) {
+                    const double a = ai[(long)j * d.lda];
 #pragma unroll
                     for (int c = 0; c < kMaxRhs; ++c)
                         if (c < nrhs) acc[c] = fma(a, xs[c * kMaxN + j], acc[c]);
@@ -456,7 +540,7 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
                 v[c * kMaxN + i] = (T)(d.R[(long)c * n + d.perm[i]] / pow2_ceil_d(sh.rnorm[c]));
             }
             __syncthreads();
-            lu_solve<T>(n, nrhs, W, ldw, v);
+            lu_solve<T>(n, nrhs, W, ldw, Dinv, v, tmp);
             for (int c = 0; c < nrhs; ++c) {
                 const double s = pow2_ceil_d(sh.rnorm[c]);
                 double zm = 0.0;
@@ -520,6 +604,7 @@ size_t batched_layout(int batch, const int *n, const int *nrhs, bool fp64, size_
         const size_t at = carve_b(off, el * (size_t)nn * ldw);
         carve_b(off, sizeof(double) * (size_t)nn * rr);
         carve_b(off, sizeof(int) * (size_t)nn);
+        carve_b(off, el * 2048 * (size_t)((nn + 31) / 32));
         if (per_sys_off) per_sys_off[b] = at;
     }
     return (off + 255) / 256 * 256;
@@ -562,6 +647,9 @@ int batched_run(int batch, const int *n, const int *nrhs, const double *const *A
         o2 += sizeof(double) * (size_t)nn * std::max(nrhs[b], 1);
         o2 = (o2 + 255) / 256 * 256;
         d.perm = reinterpret_cast<int *>(base + o2);
+        o2 += sizeof(int) * (size_t)nn;
+        o2 = (o2 + 255) / 256 * 256;
+        d.Dinv = base + o2;
     }
     // queue: non-empty systems by decreasing n^3 (longest first)
     std::vector<int> ord;

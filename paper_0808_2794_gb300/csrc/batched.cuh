@@ -13,6 +13,7 @@ struct BatchSys {
     void *W;      // n x ldw working matrix (FP32, or FP64 in the fallback pass)
     double *R;    // n x nrhs FP64 residual
     int *perm;    // composed row permutation
+    void *Dinv;   // inverses of the 32 x 32 diagonal blocks of L and U
     int iter, info;
     unsigned flags;
     int pad;

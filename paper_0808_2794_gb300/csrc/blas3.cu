@@ -1,6 +1,7 @@
 // blas3.cu -- row exchanges, SIMT GEMM update and small triangular solves
 // used inside the blocked factorization (Section 3.1.1: the SGETRF building
 // blocks; Section 2.1: PA = LU).  All matrices are row-major.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -378,51 +379,58 @@ template cudaError_t launch_gemm_batched<double>(int, int, int, double, double, 
 // ============================================================================
 namespace {
 
+// B[m x N] <- L^{-1} B (m <= 64, L unit lower).  A CTA of 256 threads owns
+// 64 columns of B; thread (q, c) holds rows 16q..16q+15 of column c.  Row
+// blocks are finished in order: the owners of block q solve its 16 x 16
+// diagonal triangle in registers and publish the values, then the owners of
+// the later blocks subtract that block's contribution (16 independent
+// accumulators per thread).  The published block is double-buffered: the
+// writer of block q+1 cannot overwrite block q-1's values before every
+// thread has passed the barrier after block q.
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 trsm_llnu_small_kernel(int m, int N, const T *__restrict__ L, long ldl, T *__restrict__ B, long ldb) {
-    __shared__ T Ls[64][64];
+    __shared__ T Ls[64][64];     // read as broadcasts (a warp shares q)
+    __shared__ T Xs[2][16][64];  // the finished row block, double-buffered
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
         const int i = idx / 64, l = idx % 64;
         Ls[i][l] = (i < m && l < i) ? L[(long)i * ldl + l] : T(0);
     }
+    const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
+    const int col = blockIdx.x * 64 + c;
+    const bool cv = col < N;
+    T b[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int r = q * 16 + i;
+        b[i] = (cv && r < m) ? B[(long)r * ldb + col] : T(0);
+    }
     __syncthreads();
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= N) return;
-    // rows 0..31: forward substitution with the top-left triangle
-    T b0[32];
+#pragma unroll 1
+    for (int qb = 0; qb < 4; ++qb) {
+        if (q == qb) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) b0[i] = (i < m) ? B[(long)i * ldb + col] : T(0);
+            for (int i = 1; i < 16; ++i)
 #pragma unroll
-    for (int i = 1; i < 32; ++i) {
-        T s = b0[i];
+                for (int l = 0; l < i; ++l) b[i] = fma(-Ls[qb * 16 + i][qb * 16 + l], b[l], b[i]);
 #pragma unroll
-        for (int l = 0; l < i; ++l) s = fma(-Ls[i][l], b0[l], s);
-        b0[i] = s;
+            for (int i = 0; i < 16; ++i) Xs[qb & 1][i][c] = b[i];
+        }
+        __syncthreads();
+        if (q > qb) {
+#pragma unroll
+            for (int l = 0; l < 16; ++l) {
+                const T x = Xs[qb & 1][l][c];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) b[i] = fma(-Ls[q * 16 + i][qb * 16 + l], x, b[i]);
+            }
+        }
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-        if (i < m) B[(long)i * ldb + col] = b0[i];
-    if (m <= 32) return;
-    // rows 32..63: subtract the off-diagonal block, then the bottom-right triangle
-    T b1[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        T s = (32 + i < m) ? B[(long)(32 + i) * ldb + col] : T(0);
-#pragma unroll
-        for (int l = 0; l < 32; ++l) s = fma(-Ls[32 + i][l], b0[l], s);
-        b1[i] = s;
+    for (int i = 0; i < 16; ++i) {
+        const int r = q * 16 + i;
+        if (cv && r < m) B[(long)r * ldb + col] = b[i];
     }
-#pragma unroll
-    for (int i = 1; i < 32; ++i) {
-        T s = b1[i];
-#pragma unroll
-        for (int l = 0; l < i; ++l) s = fma(-Ls[32 + i][32 + l], b1[l], s);
-        b1[i] = s;
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        if (32 + i < m) B[(long)(32 + i) * ldb + col] = b1[i];
 }
 
 }  // namespace
@@ -432,7 +440,7 @@ cudaError_t launch_trsm_llnu_small(int m, int N, const T *L, long ldl, T *B, lon
     if (m <= 0 || N <= 0) return cudaSuccess;
     if (m > 64) return cudaErrorInvalidValue;
     mp_note_launch();
-    trsm_llnu_small_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(m, N, L, ldl, B, ldb);
+    trsm_llnu_small_kernel<T><<<(N + 63) / 64, 256, 0, s>>>(m, N, L, ldl, B, ldb);
     return cudaGetLastError();
 }
 template cudaError_t launch_trsm_llnu_small<float>(int, int, const float *, long, float *, long, cudaStream_t);

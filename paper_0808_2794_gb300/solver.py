@@ -331,44 +331,63 @@ _SOLVE_FN = None
 BATCH_MAX_N = 512
 
 
-def gesv_batched(As, Bs, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True, work=None,
-                 stream=None):
+class BatchedPlan:
+    """Argument tables of one batch (host arrays of sizes and device pointers)
+    prepared once, so that repeated solves of the same batch only make the C
+    call.  Outputs X, ipiv are allocated here and reused by every run()."""
+
+    def __init__(self, As, Bs, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True):
+        import numpy as np
+        torch = _torch()
+        self.lib = load()
+        count = len(As)
+        self.count = count
+        self.A_c = [colmajor(a) for a in As]
+        self.B_c = [colmajor(b) for b in Bs]
+        self.vec = [b.dim() == 1 for b in Bs]
+        self.n = np.array([a.shape[0] for a in self.A_c], dtype=np.int32)
+        self.nrhs = np.array([b.shape[1] for b in self.B_c], dtype=np.int32)
+        self.X_c = [torch.empty((int(r), int(m)), dtype=torch.float64, device=a.device).t()
+                    for a, m, r in zip(self.A_c, self.n, self.nrhs)]
+        self.piv = [torch.zeros(max(int(m), 1), dtype=torch.int32, device=a.device)
+                    for a, m in zip(self.A_c, self.n)]
+        self.lda = np.array([_ld(a) for a in self.A_c], dtype=np.int32)
+        self.ldb = np.array([_ld(b) for b in self.B_c], dtype=np.int32)
+        self.ldx = np.array([_ld(x) for x in self.X_c], dtype=np.int32)
+        self.pa = np.array([a.data_ptr() for a in self.A_c], dtype=np.uint64)
+        self.pb = np.array([b.data_ptr() for b in self.B_c], dtype=np.uint64)
+        self.px = np.array([x.data_ptr() for x in self.X_c], dtype=np.uint64)
+        self.pp = np.array([p.data_ptr() for p in self.piv], dtype=np.uint64)
+        self.iter = np.zeros(count, dtype=np.int32)
+        self.flags = np.zeros(count, dtype=np.uint32)
+        self.info = np.zeros(count, dtype=np.int32)
+        self.opts = default_opts(prec=prec, itermax=itermax, tol=tol,
+                                 allow_fallback=int(bool(allow_fallback)))
+        need = self.lib.mp_gesv_batched_workspace_bytes(count, self.n.ctypes.data, self.nrhs.ctypes.data,
+                                                        ctypes.byref(self.opts))
+        self.work = workspace(need, self.A_c[0].device if count else None)
+
+    def run(self, stream=None):
+        ret = self.lib.mp_gesv_batched(
+            self.count, self.n.ctypes.data, self.nrhs.ctypes.data, self.pa.ctypes.data, self.lda.ctypes.data,
+            self.pb.ctypes.data, self.ldb.ctypes.data, self.px.ctypes.data, self.ldx.ctypes.data,
+            self.pp.ctypes.data, self.iter.ctypes.data, self.flags.ctypes.data, self.info.ctypes.data,
+            self.work.data_ptr(), self.work.numel(), ctypes.byref(self.opts), _stream_ptr(stream))
+        _check(ret, "mp_gesv_batched")
+        return self
+
+    def results(self):
+        Xs = [x[:, 0] if v else x for x, v in zip(self.X_c, self.vec)]
+        return Xs, [p[:int(m)] for p, m in zip(self.piv, self.n)], self.iter, self.flags, self.info
+
+
+def gesv_batched(As, Bs, prec="fp32", itermax=30, tol=1e-14, allow_fallback=True, stream=None):
     """Solve the independent systems As[i] X_i = Bs[i] (n_i <= 512) in one
     persistent launch.  As, Bs: sequences of float64 CUDA tensors (B_i of
     shape (n_i,) or (n_i, nrhs_i)).  Returns (Xs, ipivs, iter, flags, info)
     with iter/flags/info numpy arrays."""
-    import numpy as np
-    torch = _torch()
-    lib = load()
-    count = len(As)
-    A_c = [colmajor(a) for a in As]
-    B_c = [colmajor(b) for b in Bs]
-    n = np.array([a.shape[0] for a in A_c], dtype=np.int32)
-    nrhs = np.array([b.shape[1] for b in B_c], dtype=np.int32)
-    X_c = [torch.empty((int(r), int(m)), dtype=torch.float64, device=a.device).t()
-           for a, m, r in zip(A_c, n, nrhs)]
-    piv = [torch.zeros(max(int(m), 1), dtype=torch.int32, device=a.device) for a, m in zip(A_c, n)]
-    lda = np.array([_ld(a) for a in A_c], dtype=np.int32)
-    ldb = np.array([_ld(b) for b in B_c], dtype=np.int32)
-    ldx = np.array([_ld(x) for x in X_c], dtype=np.int32)
-    pa = np.array([a.data_ptr() for a in A_c], dtype=np.uint64)
-    pb = np.array([b.data_ptr() for b in B_c], dtype=np.uint64)
-    px = np.array([x.data_ptr() for x in X_c], dtype=np.uint64)
-    pp = np.array([p.data_ptr() for p in piv], dtype=np.uint64)
-    it = np.zeros(count, dtype=np.int32)
-    fl = np.zeros(count, dtype=np.uint32)
-    info = np.zeros(count, dtype=np.int32)
-    opts = default_opts(prec=prec, itermax=itermax, tol=tol, allow_fallback=int(bool(allow_fallback)))
-    need = lib.mp_gesv_batched_workspace_bytes(count, n.ctypes.data, nrhs.ctypes.data, ctypes.byref(opts))
-    if work is None or work.numel() < need:
-        work = workspace(need, A_c[0].device if count else None)
-    ret = lib.mp_gesv_batched(count, n.ctypes.data, nrhs.ctypes.data, pa.ctypes.data, lda.ctypes.data,
-                              pb.ctypes.data, ldb.ctypes.data, px.ctypes.data, ldx.ctypes.data,
-                              pp.ctypes.data, it.ctypes.data, fl.ctypes.data, info.ctypes.data,
-                              work.data_ptr(), work.numel(), ctypes.byref(opts), _stream_ptr(stream))
-    _check(ret, "mp_gesv_batched")
-    Xs = [x[:, 0] if b.dim() == 1 else x for x, b in zip(X_c, Bs)]
-    return Xs, [p[:int(m)] for p, m in zip(piv, n)], it, fl, info
+    plan = BatchedPlan(As, Bs, prec=prec, itermax=itermax, tol=tol, allow_fallback=allow_fallback)
+    return plan.run(stream).results()
 
 
 def gesv_host(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
