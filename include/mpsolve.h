@@ -84,7 +84,7 @@ typedef struct {
     double gmres_tol;    /* relative inner residual target (default 1e-6) */
     double stall_ratio;  /* stall if ||z_k|| > stall_ratio * ||z_{k-1}|| (default 0.5) */
     int allow_fallback;  /* re-factor in FP64 on breakdown/stall/non-convergence (default 1) */
-    int nb_outer;        /* outer block width of the factorization (0 = auto) */
+    int nb_outer;        /* outer block width of the factorization (0 = auto; 32..1024) */
     int nb_inner;        /* reserved (0 = auto) */
 } mp_opts;
 

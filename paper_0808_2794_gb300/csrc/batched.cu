@@ -577,7 +577,7 @@ cudaError_t launch_batched(BatchSys *dsys, const int *dorder, int count, int *dc
     if (count <= 0) return cudaSuccess;
     const size_t smem = batched_smem_bytes<T>();
     auto kern = batched_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

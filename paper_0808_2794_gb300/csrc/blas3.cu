@@ -3,6 +3,7 @@
 // blocks; Section 2.1: PA = LU).  All matrices are row-major.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -115,6 +116,140 @@ apply_moves_kernel(T *__restrict__ W, long ld, const int2 *__restrict__ pairs,
     }
 }
 
+// One leaf step of the panel factorization, after the leaf (columns
+// [k, k+kb)) has been factored and its rows exchanged:
+//   U = X A12, X = L11^{-1} from the panel kernel
+//                     (A12: rows k..k+kb of the columns [k+kb, k+kb+N))
+//   A22 -= L21 U      (rows [k+kb, k+kb+M) of the same columns)
+// in one launch over (64-row tile, 128-column chunk) pairs.  Columns of U
+// are independent, so every CTA forms the U columns of its chunk in shared
+// memory (the same arithmetic in each CTA of a chunk, so all copies agree
+// bit for bit) and updates its 64 x 128 tile of A22 with FP32 (FP64)
+// FMAs in the order l = 0..kb-1.  The CTA that draws the last ticket of a
+// chunk, i.e. after every CTA of that chunk has read its A12 columns, writes
+// them back as U and resets the ticket.  No CTA waits for another.
+constexpr int kLeafTileRows = 64;
+constexpr int kLeafTileCols = 128;
+
+template <typename T, int KBMAX>
+__global__ void __launch_bounds__(256)
+leaf_update_kernel(T *W, long ld, int k, int kb, int N, int M, const T *__restrict__ X, int xs,
+                   unsigned *tickets) {
+    __shared__ __align__(16) T Us[KBMAX][kLeafTileCols];
+    __shared__ T Ls[KBMAX][KBMAX + 1];  // X = L11^{-1} (unit lower)
+    __shared__ T Lt[kLeafTileRows][KBMAX + 1];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * kLeafTileRows;
+    const int chunk = blockIdx.y, c0 = chunk * kLeafTileCols;
+    const int w = min(kLeafTileCols, N - c0);
+    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+        const int i = idx / kb, l = idx - i * kb;
+        Ls[i][l] = l < i ? X[i * xs + l] : T(0);
+    }
+    for (int idx = tid; idx < kb * kLeafTileCols; idx += blockDim.x) {
+        const int i = idx / kLeafTileCols, c = idx - i * kLeafTileCols;
+        Us[i][c] = c < w ? W[(long)(k + i) * ld + k + kb + c0 + c] : T(0);
+    }
+    for (int idx = tid; idx < kLeafTileRows * kb; idx += blockDim.x) {
+        const int r = idx / kb, l = idx - r * kb;
+        Lt[r][l] = r0 + r < M ? W[(long)(k + kb + r0 + r) * ld + k + l] : T(0);
+    }
+    // this thread's 8 rows x 4 columns of the A22 tile, loaded early (16-byte
+    // vectors when the 4 columns are inside the tile: the tile starts on a
+    // multiple of 4 columns and ld is a multiple of 32)
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const int ty = tid >> 5, tx = tid & 31;
+    const bool full4 = tx * 4 + 3 < w;
+    T acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = r0 + ty * 8 + a;
+        const T *src = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
+        if (r < M && full4) {
+#pragma unroll
+            for (int q = 0; q < 4 / VW; ++q) {
+                const V v = reinterpret_cast<const V *>(src)[q];
+                const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = (r < M && tx * 4 + b < w) ? src[b] : T(0);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(&tickets[chunk], 1u) == gridDim.x - 1;
+    }
+    // U = X A12 for the chunk's columns: thread (g, c) forms rows g, g+2, ...
+    // of column c (independent dot products, l in order)
+    {
+        const int c = tid & (kLeafTileCols - 1), g = tid >> 7;
+        T u[(KBMAX + 1) / 2];
+#pragma unroll
+        for (int q = 0; q < (KBMAX + 1) / 2; ++q) {
+            const int i = g + 2 * q;
+            T v = i < kb ? Us[i][c] : T(0);
+            for (int l = 0; l < i; ++l) v = fma(Ls[i][l], Us[l][c], v);
+            u[q] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < (KBMAX + 1) / 2; ++q) {
+            const int i = g + 2 * q;
+            if (i < kb) Us[i][c] = u[q];
+        }
+    }
+    __syncthreads();
+    if (last) {
+        for (int idx = tid; idx < kb * kLeafTileCols; idx += blockDim.x) {
+            const int i = idx / kLeafTileCols, c = idx - i * kLeafTileCols;
+            if (c < w) W[(long)(k + i) * ld + k + kb + c0 + c] = Us[i][c];
+        }
+        if (tid == 0) tickets[chunk] = 0u;
+    }
+    for (int l = 0; l < kb; ++l) {
+        T bv[4], av[8];
+#pragma unroll
+        for (int q = 0; q < 4 / VW; ++q) {
+            const V v = reinterpret_cast<const V *>(&Us[l][tx * 4])[q];
+            const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) bv[q * VW + e] = pv[e];
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) av[a] = Lt[ty * 8 + a][l];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = r0 + ty * 8 + a;
+        if (r >= M) continue;
+        T *dst = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
+        if (full4) {
+#pragma unroll
+            for (int q = 0; q < 4 / VW; ++q) {
+                V v;
+                T *pv = reinterpret_cast<T *>(&v);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) pv[e] = acc[a][q * VW + e];
+                reinterpret_cast<V *>(dst)[q] = v;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (tx * 4 + b < w) dst[b] = acc[a][b];
+        }
+    }
+}
+
 __global__ void apply_moves_vec_kernel(int *v, const int2 *pairs, const int *npairs) {
     extern __shared__ int vals[];
     const int np = *npairs;
@@ -131,14 +266,29 @@ cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int
     if (npiv <= 0) return cudaSuccess;
     size_t smem = sizeof(int) * (size_t)npiv;
     if (rows <= kComposeSmemRows) smem += sizeof(int) * (size_t)rows;
-    cudaError_t e = cudaFuncSetAttribute(compose_swaps_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(compose_swaps_kernel, smem);
     if (e != cudaSuccess) return e;
     mp_note_launch();
     compose_swaps_kernel<<<1, kComposeThreads, smem, s>>>(ipiv, k1, k2, n, pairs, npairs,
                                                           map_scratch);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int N, int M, const T *X, int xs, unsigned *tickets,
+                               cudaStream_t s) {
+    constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
+    if (N <= 0 || kb <= 0 || M < 0) return cudaSuccess;
+    if (kb > KBMAX || N > 1024) return cudaErrorInvalidValue;
+    dim3 grid(std::max(1, (M + kLeafTileRows - 1) / kLeafTileRows), (N + kLeafTileCols - 1) / kLeafTileCols);
+    mp_note_launch();
+    leaf_update_kernel<T, KBMAX><<<grid, 256, 0, s>>>(W, ld, k, kb, N, M, X, xs, tickets);
+    return cudaGetLastError();
+}
+template cudaError_t launch_leaf_update<float>(float *, long, int, int, int, int, const float *, int, unsigned *,
+                                              cudaStream_t);
+template cudaError_t launch_leaf_update<double>(double *, long, int, int, int, int, const double *, int, unsigned *,
+                                               cudaStream_t);
 
 template <typename T>
 cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
@@ -154,7 +304,7 @@ cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npai
     }
     size_t smem = (size_t)max_pairs * CW * sizeof(T);
     auto kern = apply_moves_kernel<T, CW>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     mp_note_launch();
     kern<<<nch, 256, smem, s>>>(W, ld, pairs, npairs, c0, c1, c2, c3, perm);

@@ -153,7 +153,7 @@ cudaError_t launch_potrf_leaf(int n, int k0, int nc, T *W, long ldw, MpDevStatus
     const int grid = below > 0 ? (below + kLeafRows - 1) / kLeafRows : 1;
     const size_t smem = sizeof(T) * kLeafRows * (kLeaf + 1);
     auto kern = potrf_leaf_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     mp_note_launch();
     kern<<<grid, kLeafRows, smem, s>>>(n, k0, nc, W, ldw, st);

@@ -123,5 +123,16 @@ struct MpProfScope {
     ~MpProfScope();
 };
 
+// cudaFuncSetAttribute for one kernel on the current device, skipped when
+// the same or a larger value was already set there (the host-side cost of the
+// call is paid once per kernel, not once per launch).  attr: a
+// cudaFuncAttribute; value: its value.
+cudaError_t mp_func_attr_once(const void *kern, cudaFuncAttribute attr, int value);
+template <typename K>
+inline cudaError_t mp_smem_attr(K kern, size_t bytes) {
+    return mp_func_attr_once(reinterpret_cast<const void *>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+}
+
 static inline int div_up(int a, int b) { return (a + b - 1) / b; }
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -11,10 +11,12 @@ template <typename T> int panel_base_width(int m);
 // ncols <= panel_base_width<T>(m).  ipiv[j] (j < ncols) receives the global
 // 1-based pivot row row0 + p + 1; moves[0 .. *nmoves) receives the composed
 // row permutation of the panel as (destination row, source row) pairs
-// (global row indices, at most 2 * ncols).
+// (global row indices, at most 2 * ncols).  linv (optional): receives the
+// inverse of the unit-lower ncols x ncols L11, row-major with stride
+// panel_base_width<T>(m).
 template <typename T>
 cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                         int *nmoves, MpDevStatus *st, cudaStream_t s);
+                         int *nmoves, MpDevStatus *st, T *linv, cudaStream_t s);
 
 // ---- row exchanges (blas3.cu) ---------------------------------------------
 // Composes the swaps ipiv[k1..k2) (1-based rows) into a list of (dst, src)
@@ -27,6 +29,14 @@ cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int
 template <typename T>
 cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,
                                int c0, int c1, int c2, int c3, int *perm, cudaStream_t s);
+// After a factored leaf (columns [k, k+kb), rows exchanged): U = X A12 with
+// X = L11^{-1} (from the panel kernel, row-major with stride xs) on rows
+// k..k+kb of the N columns right of it, and A22 -= L21 U on the M rows
+// below, in one launch (kb <= 24 FP32 / 8 FP64, N <= 1024).  tickets: one
+// device word per 128 columns, zero before the first launch (left zero).
+template <typename T>
+cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int N, int M, const T *X, int xs, unsigned *tickets,
+                               cudaStream_t s);
 // Applies the moves to an int vector (the running row permutation).
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s);

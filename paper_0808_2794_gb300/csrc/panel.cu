@@ -156,7 +156,7 @@ struct PanelSmem {
 template <typename T, int NB, int RPT, int NT>
 __global__ void __launch_bounds__(NT, 1)
 panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32_t *__restrict__ ipiv,
-                   int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st) {
+                   int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st, T *__restrict__ linv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<PanelSmem<T, NB, NT, RPT> *>(smem_raw);
     constexpr int NW = NT / 32;
@@ -192,8 +192,27 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
         gi[s] = valid ? g : INT_MAX;
         orig[s] = g;
         const T *row = P + (long)g * ld;
+        // 16-byte loads for the whole 16-byte chunks inside ncols (rows and the
+        // panel start are 16-byte aligned: ld and the column offset are
+        // multiples of 4 floats / 2 doubles), scalar loads for the rest
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int VW = 16 / sizeof(T);
+        const bool vec_ok = (reinterpret_cast<uintptr_t>(row) & 15) == 0;
 #pragma unroll
-        for (int k = 0; k < NB; ++k) a[s][k] = (valid && k < ncols) ? row[k] : T(0);
+        for (int q = 0; q < NB / VW; ++q) {
+            if (valid && vec_ok && (q + 1) * VW <= ncols) {
+                const V v = reinterpret_cast<const V *>(row)[q];
+                const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) a[s][q * VW + e] = pv[e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int k = q * VW + e;
+                    a[s][k] = (valid && k < ncols) ? row[k] : T(0);
+                }
+            }
+        }
     }
 
     bool ok = true;
@@ -372,13 +391,42 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
     }
     if (!ok) mp_flag(st, MP_FLAG_TIMEOUT);
     __syncthreads();
+    // X = L11^{-1} (unit lower, ncols x ncols; rows 0..ncols-1 are local rows
+    // of CTA 0), row-major with stride NB: thread c forms column c by
+    // substitution, x_i = -sum_{c<=l<i} l_il x_l, x_c = 1
+    if (linv && rank == 0 && tid < ncols) {
+        const int c = tid;
+        T x[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            T v = T(i == c ? 1 : 0);
+#pragma unroll
+            for (int l = 0; l < i; ++l)
+                if (l >= c) v = fma(-sm.fin[i][l], x[l], v);
+            x[i] = (i < c || i >= ncols) ? T(0) : v;
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+            if (i < ncols) linv[i * NB + c] = x[i];
+    }
     // write back the finished rows and the composed permutation
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
         if (gi[s] < m) {
             T *row = P + (long)gi[s] * ld;
             const T *f = sm.fin[tid + s * NT];
-            for (int k = 0; k < ncols; ++k) row[k] = f[k];
+            using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            constexpr int VW = 16 / sizeof(T);
+            int k = 0;
+            if ((reinterpret_cast<uintptr_t>(row) & 15) == 0)
+                for (; k + VW <= ncols; k += VW) {
+                    V v;
+                    T *pv = reinterpret_cast<T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) pv[e] = f[k + e];
+                    *reinterpret_cast<V *>(row + k) = v;
+                }
+            for (; k < ncols; ++k) row[k] = f[k];
             if (orig[s] != gi[s]) {
                 const int slot = atomicAdd(nmoves, 1);
                 moves[slot] = make_int2(row0 + gi[s], row0 + orig[s]);
@@ -391,17 +439,17 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
 
 template <typename T, int NB, int RPT>
 cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                           int *nmoves, MpDevStatus *st, cudaStream_t s) {
+                           int *nmoves, MpDevStatus *st, T *linv, cudaStream_t s) {
     constexpr int NT = 512;
     const int cap = NT * RPT;
     const int CL = (m + cap - 1) / cap;
     if (CL < 1 || CL > 16 || ncols > NB || ncols < 1 || m < ncols) return cudaErrorInvalidValue;
     auto kern = panel_getf2_kernel<T, NB, RPT, NT>;
     const size_t smem = sizeof(PanelSmem<T, NB, NT, RPT>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = mp_func_attr_once(reinterpret_cast<const void *>(kern), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -417,7 +465,7 @@ cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     mp_note_launch();
-    return cudaLaunchKernelEx(&cfg, kern, P, ld, m, ncols, row0, ipiv, moves, nmoves, st);
+    return cudaLaunchKernelEx(&cfg, kern, P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv);
 }
 
 }  // namespace
@@ -442,15 +490,15 @@ int panel_base_width<double>(int m) {
 
 template <>
 cudaError_t launch_panel<float>(float *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                                int *nmoves, MpDevStatus *st, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<float, 24, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
-    if (m <= 32768) return launch_panel_t<float, 16, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
-    return launch_panel_t<float, 8, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
+                                int *nmoves, MpDevStatus *st, float *linv, cudaStream_t s) {
+    if (m <= 16384) return launch_panel_t<float, 24, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+    if (m <= 32768) return launch_panel_t<float, 16, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+    return launch_panel_t<float, 8, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
 }
 template <>
 cudaError_t launch_panel<double>(double *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                                 int *nmoves, MpDevStatus *st, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<double, 8, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
-    if (m <= 32768) return launch_panel_t<double, 8, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
-    return launch_panel_t<double, 4, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, s);
+                                 int *nmoves, MpDevStatus *st, double *linv, cudaStream_t s) {
+    if (m <= 16384) return launch_panel_t<double, 8, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+    if (m <= 32768) return launch_panel_t<double, 8, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+    return launch_panel_t<double, 4, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
 }

@@ -44,18 +44,15 @@ residual_partial_kernel(int n, int nrhs, const double *__restrict__ A, long lda,
     for (int c = 0; c < NR; ++c) acc[c] = 0.0;
     const double *a = A + (long)c0 * lda + row;
     int j = 0;
-    for (; j + 4 <= len; j += 4) {
-        const double a0 = __ldcs(a + (long)(j + 0) * lda);
-        const double a1 = __ldcs(a + (long)(j + 1) * lda);
-        const double a2 = __ldcs(a + (long)(j + 2) * lda);
-        const double a3 = __ldcs(a + (long)(j + 3) * lda);
+    // 8 column loads in flight per thread (the products keep column order)
+    for (; j + 8 <= len; j += 8) {
+        double av[8];
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            acc[c] = fma(a0, xsf[(j + 0) * NR + c], acc[c]);
-            acc[c] = fma(a1, xsf[(j + 1) * NR + c], acc[c]);
-            acc[c] = fma(a2, xsf[(j + 2) * NR + c], acc[c]);
-            acc[c] = fma(a3, xsf[(j + 3) * NR + c], acc[c]);
-        }
+        for (int t = 0; t < 8; ++t) av[t] = __ldcs(a + (long)(j + t) * lda);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[c] = fma(av[t], xsf[(j + t) * NR + c], acc[c]);
     }
     for (; j < len; ++j) {
         const double a0 = a[(long)j * lda];

@@ -82,6 +82,29 @@ MpProfScope::~MpProfScope() {
     g_prof.push_back({cls, work, e0, e1});
 }
 
+cudaError_t mp_func_attr_once(const void *kern, cudaFuncAttribute attr, int value) {
+    struct Entry {
+        const void *k;
+        int attr, dev, value;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> seen;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    for (auto &x : seen)
+        if (x.k == kern && x.attr == (int)attr && x.dev == dev) {
+            if (x.value >= value) return cudaSuccess;
+            e = cudaFuncSetAttribute(kern, attr, value);
+            if (e == cudaSuccess) x.value = value;
+            return e;
+        }
+    e = cudaFuncSetAttribute(kern, attr, value);
+    if (e == cudaSuccess) seen.push_back({kern, (int)attr, dev, value});
+    return e;
+}
+
 extern "C" void mp_profile_enable(unsigned mask) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     for (auto &r : g_prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -143,7 +166,7 @@ struct StatusBlock {
 enum FactorKind { kNoFactors = 0, kLuF32 = 1, kLuF64 = 2, kCholF32 = 3, kCholF64 = 4 };
 
 int outer_nb(int n, const mp_opts &o) {
-    if (o.nb_outer > 0) return std::max(32, o.nb_outer / 32 * 32);
+    if (o.nb_outer > 0) return std::min(1024, std::max(32, o.nb_outer / 32 * 32));
     if (o.prec == MP_PREC_FP32) return n >= 4096 ? 256 : 128;
     return n >= 8192 ? 512 : 256;
 }
@@ -153,7 +176,7 @@ int outer_nb(int n, const mp_opts &o) {
 // ---------------------------------------------------------------------------
 struct Layout {
     size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, R, Y, Z,
-        part, tc, gV, gZ, gsm, total;
+        part, tc, linv, gV, gZ, gsm, total;
     size_t W_bytes;
     int ldw, nblk, ksplit, nb;
 };
@@ -182,7 +205,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.ipiv = carve(off, sizeof(int) * (size_t)n);
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, L.nb));
-    L.npairs = carve(off, sizeof(int) * 4);
+    L.npairs = carve(off, sizeof(int) * 16);  // [0]: move count, [4..12): leaf tickets
     L.map = carve(off, sizeof(int) * (size_t)n);
     const size_t inv_bytes = std::max(trsv_inverse_bytes<float>(n), fp64_space ? trsv_inverse_bytes<double>(n) : 0);
     L.Linv = carve(off, inv_bytes);
@@ -198,6 +221,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
                                              : std::max(tc_workspace_bytes(n, L.nb, o.prec),
                                                         tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
+    L.linv = carve(off, 32 * 32 * sizeof(double));  // a leaf's L11^{-1}
     // GMRES: Krylov basis V (m+1 columns), preconditioned vectors Z (m), small vectors
     const size_t m = o.refine == MP_REFINE_CLASSICAL ? 0 : (size_t)std::max(o.gmres_restart, 1);
     L.gV = carve(off, m ? sizeof(double) * (size_t)n * (m + 1) : 0);
@@ -239,6 +263,7 @@ struct FactorCtx {
     cudaStream_t s;
     int prec;
     void *tc;
+    T *linv;  // inverse of the last leaf's L11 (panel_base_width^2 elements)
 };
 
 #define CU(expr)                                      \
@@ -273,36 +298,37 @@ cudaError_t trsm_rec(FactorCtx<T> &c, int m, int N, const T *L, long ldl, T *B, 
     return trsm_rec<T>(c, m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb);
 }
 
-// Recursive LU of the columns [k0, k0+ncols) of rows [k0, n) (a recursive
-// panel): left half, U12 = L11^{-1} A12 and A22 -= L21 U12 (FP32) on the
-// right half, right half.  A leaf (ncols <= base width) is one cluster panel
-// kernel followed by the exchange of its rows over all other columns of W
-// (and the running row permutation), so every level sees rows in the
-// current pivoted order.
+// LU of the outer panel, columns [k0, k0+ncols) of rows [k0, n), leaf by
+// leaf (right-looking inside the panel): a leaf of at most the base width
+// is one cluster panel kernel, followed by the exchange of its rows over all
+// other columns of W (and the running row permutation) and by one fused
+// launch that forms the leaf's rows of U for the rest of the panel and
+// updates the rows below (FP32 FMA; FP64 in the fallback).
 template <typename T>
-cudaError_t getrf_rec(FactorCtx<T> &c, int k0, int ncols) {
-    const int m = c.n - k0;
-    const int nb = panel_base_width<T>(m);
+cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
     T *W = c.W;
     const long ld = c.ld;
-    if (ncols <= nb) {
+    unsigned *ticket = reinterpret_cast<unsigned *>(c.npairs + 4);  // one per 128-column chunk
+    for (int k = k0; k < k0 + ncols;) {
+        const int m = c.n - k;
+        const int kb = std::min(panel_base_width<T>(m), k0 + ncols - k);
         {
-            MpProfScope ps(MP_KC_PANEL, (double)m * ncols * ncols - (double)ncols * ncols * ncols / 3.0, c.s);
-            CU(launch_panel<T>(W + (long)k0 * ld + k0, ld, m, ncols, k0, c.ipiv + k0, c.pairs, c.npairs, c.st, c.s));
+            MpProfScope ps(MP_KC_PANEL, (double)m * kb * kb - (double)kb * kb * kb / 3.0, c.s);
+            CU(launch_panel<T>(W + (long)k * ld + k, ld, m, kb, k, c.ipiv + k, c.pairs, c.npairs, c.st, c.linv,
+                               c.s));
         }
-        MpProfScope ps(MP_KC_ROWMOVES, 4.0 * ncols * (double)(c.n - ncols) * sizeof(T), c.s);
-        return launch_apply_moves<T>(W, ld, c.pairs, c.npairs, 2 * ncols, 0, k0, k0 + ncols, c.n, c.perm, c.s);
+        {
+            MpProfScope ps(MP_KC_ROWMOVES, 4.0 * kb * (double)(c.n - kb) * sizeof(T), c.s);
+            CU(launch_apply_moves<T>(W, ld, c.pairs, c.npairs, 2 * kb, 0, k, k + kb, c.n, c.perm, c.s));
+        }
+        const int N = k0 + ncols - k - kb;
+        if (N > 0) {
+            MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * N + 2.0 * (m - kb) * N * kb, c.s);
+            CU(launch_leaf_update<T>(W, ld, k, kb, N, m - kb, c.linv, panel_base_width<T>(m), ticket, c.s));
+        }
+        k += kb;
     }
-    int n1 = (ncols / 2) / nb * nb;
-    if (n1 < nb) n1 = nb;
-    CU(getrf_rec<T>(c, k0, n1));
-    {
-        MpProfScope ps(MP_KC_PANELGEMM, (double)n1 * n1 * (ncols - n1) + 2.0 * (m - n1) * (ncols - n1) * n1, c.s);
-        CU(trsm_rec<T>(c, n1, ncols - n1, W + (long)k0 * ld + k0, ld, W + (long)k0 * ld + k0 + n1, ld));
-        CU(gemm_fp32_accurate<T>(c, m - n1, ncols - n1, n1, W + (long)(k0 + n1) * ld + k0, ld,
-                                 W + (long)k0 * ld + k0 + n1, ld, W + (long)(k0 + n1) * ld + k0 + n1, ld));
-    }
-    return getrf_rec<T>(c, k0 + n1, ncols - n1);
+    return cudaSuccess;
 }
 
 // Blocked right-looking LU: panel of width nb (recursive, rows exchanged over
@@ -313,9 +339,10 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     const int n = c.n;
     T *W = c.W;
     const long ld = c.ld;
+    CU(cudaMemsetAsync(c.npairs + 4, 0, 8 * sizeof(int), c.s));  // the leaf-update tickets
     for (int k = 0; k < n; k += nb) {
         const int nbk = std::min(nb, n - k);
-        CU(getrf_rec<T>(c, k, nbk));
+        CU(getrf_panel<T>(c, k, nbk));
         const int rest = n - k - nbk;
         if (rest > 0) {
             {
@@ -505,7 +532,7 @@ int factor(Solve &S, int prec, int nb, int *info_out, uint32_t *flags_out) {
     MP_CUDA_TRY(launch_iota(at<int>(S.work, L.map), S.n, S.s));
     FactorCtx<T> c{W, (long)L.ldw, S.n, at<int32_t>(S.work, L.ipiv), at<int>(S.work, L.perm),
                    at<int2>(S.work, L.pairs), at<int>(S.work, L.npairs), at<int>(S.work, L.map),
-                   &S.sb->st, S.s, prec, at<void>(S.work, L.tc)};
+                   &S.sb->st, S.s, prec, at<void>(S.work, L.tc), at<T>(S.work, L.linv)};
     if (S.sym) {
         // A = L L^T; L^T mirrored into the upper triangle; the lower solve
         // uses L's own (non-unit) diagonal
@@ -1120,7 +1147,7 @@ extern "C" int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const do
 // ---------------------------------------------------------------------------
 namespace {
 struct StepLayout {
-    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, Y, Z, part, tc, total;
+    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, Y, Z, part, tc, linv, total;
     int nblk, ksplit;
 };
 StepLayout step_layout(int n, int nrhs, int nb, int prec) {
@@ -1133,7 +1160,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.rowsum = carve(off, sizeof(double) * (size_t)n);
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, nb));
-    L.npairs = carve(off, sizeof(int) * 4);
+    L.npairs = carve(off, sizeof(int) * 16);  // [0]: move count, [4..12): leaf tickets
     L.map = carve(off, sizeof(int) * (size_t)n);
     L.Linv = carve(off, trsv_inverse_bytes<float>(n));
     L.Uinv = carve(off, trsv_inverse_bytes<float>(n));
@@ -1146,6 +1173,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.tc = carve(off, prec == MP_PREC_FP32 ? 0
                                            : std::max(tc_workspace_bytes(n, nb, prec),
                                                       tc_workspace_bytes(n, nb, MP_PREC_FP16X3)));
+    L.linv = carve(off, 32 * 32 * sizeof(double));
     L.total = align_up(off, 256);
     return L;
 }
@@ -1213,7 +1241,8 @@ extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp
     MP_CUDA_TRY(launch_iota(at<int>(work, L.perm), n, s));
     MP_CUDA_TRY(launch_iota(at<int>(work, L.map), n, s));
     FactorCtx<float> c{dW, (long)ldw, n, dipiv, at<int>(work, L.perm), at<int2>(work, L.pairs),
-                       at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc)};
+                       at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc),
+                       at<float>(work, L.linv)};
     MP_CUDA_TRY(getrf_blocked<float>(c, nb));
     StatusBlock h;
     MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -336,18 +336,22 @@ pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long 
 }
 
 // Bp[i][k] = fl_p(L[i][k]) for i < M, k < Kpad (zero for k >= K); SPLIT as above.
+// One warp per row (grid-stride over rows), lanes along k.
 template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
 pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, H *__restrict__ Bp, long lo_row,
                  const float *__restrict__ scale) {
-    const long total = (long)M * Kpad;
     const float sc = SPLIT == 2 ? *scale : 1.0f;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / Kpad), k = (int)(idx - (long)i * Kpad);
-        const float v = (k < K ? L[(long)i * ldl + k] : 0.f) * sc;
-        const H hi = to_half<H>(v);
-        Bp[idx] = hi;
-        if constexpr (SPLIT == 2) Bp[lo_row * Kpad + idx] = to_half<H>(v - __half2float(hi));
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M; i += gridDim.x * (blockDim.x >> 5)) {
+        const float *src = L + (long)i * ldl;
+        H *dst = Bp + (long)i * Kpad;
+        for (int k = lane; k < Kpad; k += 32) {
+            const float v = (k < K ? src[k] : 0.f) * sc;
+            const H hi = to_half<H>(v);
+            dst[k] = hi;
+            if constexpr (SPLIT == 2) dst[lo_row * Kpad + k] = to_half<H>(v - __half2float(hi));
+        }
     }
 }
 
@@ -355,11 +359,20 @@ pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, 
 __global__ void __launch_bounds__(256)
 absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigned *out) {
     float m = 0.f;
-    const long total = (long)rows * cols;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / cols), c = (int)(idx - (long)r * cols);
-        const float v = fabsf(X[(long)r * ldx + c]);
-        m = (v > m || v != v) ? ((v != v) ? INFINITY : v) : m;
+    // work items of one row x 1024 columns, one warp each (grid-stride)
+    const int lane = threadIdx.x & 31;
+    const int chunks = (cols + 1023) / 1024;
+    const long items = (long)rows * chunks;
+    for (long it = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
+         it += (long)gridDim.x * (blockDim.x >> 5)) {
+        const int r = (int)(it / chunks), c0 = (int)(it - (long)r * chunks) * 1024;
+        const float *xr = X + (long)r * ldx;
+        const int c1 = min(cols, c0 + 1024);
+#pragma unroll 8
+        for (int c = c0 + lane; c < c1; c += 32) {
+            const float v = fabsf(xr[c]);
+            m = (v > m || v != v) ? ((v != v) ? INFINITY : v) : m;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -468,17 +481,14 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
         if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(w.umax, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
-        const long tot = (long)K * N;
         mp_note_launch();
         if (nt)
-            absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(N, K, U12, ldu, w.umax);
+            absmax_kernel<<<1216, 256, 0, s>>>(N, K, U12, ldu, w.umax);
         else
-            absmax_kernel<<<(int)std::min<long>((tot + 255) / 256, 2048L), 256, 0, s>>>(K, N, U12, ldu, w.umax);
+            absmax_kernel<<<1216, 256, 0, s>>>(K, N, U12, ldu, w.umax);
         if (nt) {
-            const long totl = (long)M * K;
             mp_note_launch();
-            absmax_kernel<<<(int)std::min<long>((totl + 255) / 256, 2048L), 256, 0, s>>>(M, K, L21, ldl,
-                                                                                        w.umax + 1);
+            absmax_kernel<<<1216, 256, 0, s>>>(M, K, L21, ldl, w.umax + 1);
         }
         mp_note_launch();
         split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales, nt ? 1 : 0);
@@ -508,7 +518,7 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     if (e != cudaSuccess) return e;
     auto kern = tc_update_kernel<FMT, SPLIT>;
     constexpr size_t smem = smem_bytes<SPLIT>();
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     const int ntiles = ((M + TILE_I - 1) / TILE_I) * ((N + TILE_J - 1) / TILE_J);
     const int grid = std::min(ntiles, num_sms());

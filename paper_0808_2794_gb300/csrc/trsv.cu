@@ -249,7 +249,7 @@ cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, con
     if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
     auto kern = trsv_persistent_kernel<T, LOWER>;
     const size_t smem = sizeof(T) * (size_t)kMaxRhs * BI;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
@@ -313,7 +313,7 @@ cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv,
     {
         auto kern = base_inverse_kernel<T, BS>;
         const size_t smem = 2 * sizeof(T) * BS * (BS + 1);
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = mp_smem_attr(kern, smem);
         if (e != cudaSuccess) return e;
         mp_note_launch();
         kern<<<(n + BS - 1) / BS, BS, smem, s>>>(n, BI, W, ldw, Linv, Uinv, lower_unit ? 1 : 0, upper_unit ? 1 : 0);
