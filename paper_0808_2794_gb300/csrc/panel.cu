@@ -120,7 +120,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 }
 // Bounded wait (about one second); false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
-    if (mbar_try(a, parity)) return true;
+    for (int i = 0; i < 64; ++i)  // the usual case: the data arrives within a few polls
+        if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long long i = 1;; ++i) {
         if (mbar_try(a, parity)) return true;

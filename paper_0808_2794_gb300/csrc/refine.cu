@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kRows)
 residual_partial_kernel(int n, int nrhs, const double *__restrict__ A, long lda,
                         const double *__restrict__ X, long ldx, double *__restrict__ part,
                         int chunk) {
-    __shared__ double xsf[kXsElems];  // chunk * NR <= kXsElems
+    __shared__ __align__(16) double xsf[kXsElems];  // chunk * NR <= kXsElems
     const int row = blockIdx.x * kRows + threadIdx.x;
     const int ks = blockIdx.y;
     const int c0 = ks * chunk;
@@ -46,13 +46,21 @@ residual_partial_kernel(int n, int nrhs, const double *__restrict__ A, long lda,
     int j = 0;
     // 8 column loads in flight per thread (the products keep column order)
     for (; j + 8 <= len; j += 8) {
-        double av[8];
+        double av[8], xv[8 * NR];
 #pragma unroll
         for (int t = 0; t < 8; ++t) av[t] = __ldcs(a + (long)(j + t) * lda);
+        // the 8 x NR values of these columns: 16-byte shared-memory loads
+        // (j is a multiple of 8, so the first value is 16-byte aligned)
+#pragma unroll
+        for (int q = 0; q < 4 * NR; ++q) {
+            const double2 v = reinterpret_cast<const double2 *>(xsf + j * NR)[q];
+            xv[2 * q] = v.x;
+            xv[2 * q + 1] = v.y;
+        }
 #pragma unroll
         for (int t = 0; t < 8; ++t)
 #pragma unroll
-            for (int c = 0; c < NR; ++c) acc[c] = fma(av[t], xsf[(j + t) * NR + c], acc[c]);
+            for (int c = 0; c < NR; ++c) acc[c] = fma(av[t], xv[t * NR + c], acc[c]);
     }
     for (; j < len; ++j) {
         const double a0 = a[(long)j * lda];
