@@ -132,7 +132,7 @@ constexpr int kLeafTileRows = 64;
 constexpr int kLeafTileCols = 128;
 
 template <typename T, int KBMAX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 leaf_update_kernel(T *W, long ld, int k, int kb, int N, int M, const T *__restrict__ X, int xs,
                    unsigned *tickets) {
     __shared__ __align__(16) T Us[KBMAX][kLeafTileCols];
@@ -154,31 +154,6 @@ leaf_update_kernel(T *W, long ld, int k, int kb, int N, int M, const T *__restri
     for (int idx = tid; idx < kLeafTileRows * kb; idx += blockDim.x) {
         const int r = idx / kb, l = idx - r * kb;
         Lt[r][l] = r0 + r < M ? W[(long)(k + kb + r0 + r) * ld + k + l] : T(0);
-    }
-    // this thread's 8 rows x 4 columns of the A22 tile, loaded early (16-byte
-    // vectors when the 4 columns are inside the tile: the tile starts on a
-    // multiple of 4 columns and ld is a multiple of 32)
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    constexpr int VW = 16 / sizeof(T);
-    const int ty = tid >> 5, tx = tid & 31;
-    const bool full4 = tx * 4 + 3 < w;
-    T acc[8][4];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int r = r0 + ty * 8 + a;
-        const T *src = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
-        if (r < M && full4) {
-#pragma unroll
-            for (int q = 0; q < 4 / VW; ++q) {
-                const V v = reinterpret_cast<const V *>(src)[q];
-                const T *pv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = (r < M && tx * 4 + b < w) ? src[b] : T(0);
-        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -211,6 +186,31 @@ leaf_update_kernel(T *W, long ld, int k, int kb, int N, int M, const T *__restri
             if (c < w) W[(long)(k + i) * ld + k + kb + c0 + c] = Us[i][c];
         }
         if (tid == 0) tickets[chunk] = 0u;
+    }
+    // this thread's 8 rows x 4 columns of the A22 tile (16-byte
+    // vectors when the 4 columns are inside the tile: the tile starts on a
+    // multiple of 4 columns and ld is a multiple of 32)
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const int ty = tid >> 5, tx = tid & 31;
+    const bool full4 = tx * 4 + 3 < w;
+    T acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = r0 + ty * 8 + a;
+        const T *src = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
+        if (r < M && full4) {
+#pragma unroll
+            for (int q = 0; q < 4 / VW; ++q) {
+                const V v = reinterpret_cast<const V *>(src)[q];
+                const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = (r < M && tx * 4 + b < w) ? src[b] : T(0);
+        }
     }
     for (int l = 0; l < kb; ++l) {
         T bv[4], av[8];
