@@ -23,29 +23,37 @@ template <typename Tout>
 __global__ void __launch_bounds__(256)
 convert_transpose_kernel(int n, const double *__restrict__ A, long lda, Tout *__restrict__ W,
                          long ldw, double *__restrict__ rowsum, MpDevStatus *st) {
-    __shared__ Tout tile[kTile][kTile + 1];
+    // 32 rows x 64 columns per step: 8 independent loads per thread in flight
+    __shared__ Tout tile[2 * kTile][kTile + 1];  // [column][row]
     __shared__ double rs[8][kTile];
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     const int r0 = blockIdx.x * kTile;
     double rsum = 0.0;
     bool bad = false;
-    for (int ct = 0; ct < kColTiles; ++ct) {
+    for (int ct = 0; ct < kColTiles; ct += 2) {
         const int c0 = (blockIdx.y * kColTiles + ct) * kTile;
         if (c0 >= n) break;
+        double v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const int c = c0 + ty + 8 * q, r = r0 + tx;
-            double v = 0.0;
-            if (r < n && c < n) v = A[(long)c * lda + r];
-            if (!(fabs(v) <= 1.79769313486231570815e308)) bad = true;
-            rsum += fabs(v);
-            tile[ty + 8 * q][tx] = cvt<Tout>(v);
+            v[q] = (r < n && c < n) ? __ldcs(A + (long)c * lda + r) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (!(fabs(v[q]) <= 1.79769313486231570815e308)) bad = true;
+            rsum += fabs(v[q]);
+            tile[ty + 8 * q][tx] = cvt<Tout>(v[q]);
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int r = r0 + ty + 8 * q, c = c0 + tx;
-            if (r < n && c < n) W[(long)r * ldw + c] = tile[tx][ty + 8 * q];
+            const int r = r0 + ty + 8 * q;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + tx + 32 * h;
+                if (r < n && c < n) W[(long)r * ldw + c] = tile[tx + 32 * h][ty + 8 * q];
+            }
         }
         __syncthreads();
     }
