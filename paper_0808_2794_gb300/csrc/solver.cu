@@ -799,7 +799,7 @@ int refine_gmres(Solve &S, const mp_opts &o, bool from_x, mp_stats *st, bool *co
 }
 
 int validate_opts(const mp_opts &o) {
-    if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_FP16) return 1;
+    if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_E4M3) return 1;
     if (o.itermax < 0 || !(o.tol > 0.0) || o.stall_ratio <= 0.0) return 1;
     if (o.refine < MP_REFINE_CLASSICAL || o.refine > MP_REFINE_AUTO) return 1;
     if (o.refine != MP_REFINE_CLASSICAL &&
@@ -1373,8 +1373,9 @@ extern "C" size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec) {
 extern "C" int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl, const float *dU,
                                    int ldu, float *dC, int ldc, void *work, size_t work_bytes, void *stream) {
     g_err[0] = 0;
-    if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3)
-        return mp_arg_fail(1, "prec must be FP32, FP16X3, BF16 or FP16");
+    if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3 &&
+        prec != MP_PREC_E4M3)
+        return mp_arg_fail(1, "prec must be FP32, FP16X3, BF16, FP16 or E4M3");
     if (M < 0) return mp_arg_fail(2, "M < 0");
     if (N < 0) return mp_arg_fail(3, "N < 0");
     if (K < 0) return mp_arg_fail(4, "K < 0");

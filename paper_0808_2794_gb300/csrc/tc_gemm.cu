@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
@@ -30,8 +31,13 @@ namespace {
 constexpr int TILE_J = 128;  // MMA M
 constexpr int TILE_I = 256;  // MMA N
 constexpr int BK = 64;       // 16-bit elements per 128-byte swizzled row
-constexpr int A_BYTES = TILE_J * BK * 2;
-constexpr int B_BYTES = TILE_I * BK * 2;
+constexpr int A_BYTES = TILE_J * 128;  // one 128-byte row of K per operand row and stage
+constexpr int B_BYTES = TILE_I * 128;
+// FMT: 0 fp16, 1 bf16 (kind::f16, 64 K-elements per stage row), 2 E4M3
+// (kind::f8f6f4, 128 K-elements per stage row); every MMA consumes 32 bytes
+// of K.  E4M3 operands carry power-of-two scales (like the split rung).
+template <uint32_t FMT> __host__ __device__ constexpr int bk_elems() { return FMT == 2 ? 128 : 64; }
+template <uint32_t FMT, int SPLIT> __host__ __device__ constexpr bool scaled() { return SPLIT == 2 || FMT == 2; }
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 64 + NUM_EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
@@ -113,6 +119,14 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
@@ -212,18 +226,19 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     const uint32_t fb = smem_u32(&bar->full[stage]);
                     mbar_expect_tx(fb, STAGE_BYTES);
                     // stage layout: A_hi [A_lo] B_hi [B_lo]
-                    tma_load_2d(sa, &mapA, kb * BK, jb * TILE_J, fb);
-                    if (SPLIT == 2) tma_load_2d(sa + A_BYTES, &mapA, kb * BK, a_lo_row + jb * TILE_J, fb);
-                    tma_load_2d(sa + SPLIT * A_BYTES, &mapB, kb * BK, ib * TILE_I, fb);
+                    constexpr int BKE = bk_elems<FMT>();
+                    tma_load_2d(sa, &mapA, kb * BKE, jb * TILE_J, fb);
+                    if (SPLIT == 2) tma_load_2d(sa + A_BYTES, &mapA, kb * BKE, a_lo_row + jb * TILE_J, fb);
+                    tma_load_2d(sa + SPLIT * A_BYTES, &mapB, kb * BKE, ib * TILE_I, fb);
                     if (SPLIT == 2)
-                        tma_load_2d(sa + SPLIT * A_BYTES + B_BYTES, &mapB, kb * BK, b_lo_row + ib * TILE_I, fb);
+                        tma_load_2d(sa + SPLIT * A_BYTES + B_BYTES, &mapB, kb * BKE, b_lo_row + ib * TILE_I, fb);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---------------- MMA issuer
-            constexpr uint32_t idesc = make_idesc(FMT);
+            constexpr uint32_t idesc = make_idesc(FMT == 2 ? 0u : FMT);  // E4M3 is format 0 of kind::f8f6f4
             int stage = 0;
             uint32_t phase = 0, acc_phase = 0;
             int acc = 0;
@@ -238,9 +253,13 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE_BYTES);
                     const uint32_t sb = sa + SPLIT * A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        umma_f16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                                 (kb | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage row
+                        if constexpr (FMT == 2)
+                            umma_f8(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                    (kb | kk) ? 1u : 0u);
+                        else
+                            umma_f16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                     (kb | kk) ? 1u : 0u);
                         if (SPLIT == 2) {  // hi*lo and lo*hi
                             umma_f16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + B_BYTES + kk * 32), idesc, 1u);
                             umma_f16(d_tmem, sw128_desc(sa + A_BYTES + kk * 32), sw128_desc(sb + kk * 32), idesc, 1u);
@@ -258,7 +277,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     } else {  // ------------------------------ epilogue warps 2..9
         const int quarter = warp & 3;        // TMEM lanes this warp may access
         const int half = (warp - 2) >> 2;    // which 128 of the 256 accumulator columns
-        const float inv_scale = SPLIT == 2 ? *inv_scale_p : 1.0f;
+        const float inv_scale = scaled<FMT, SPLIT>() ? *inv_scale_p : 1.0f;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -305,6 +324,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 template <typename H> __device__ __forceinline__ H to_half(float v);
 template <> __device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
+// E4M3: round to nearest even, saturated to +-448 (OCP FP8)
+template <> __device__ __forceinline__ __nv_fp8_e4m3 to_half<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
 
 // Ap[j][k] = fl_p(U[k][j]) for j < N, k < Kpad (zero for k >= K): 32x32 transpose.
 // SPLIT == 2: Ap[j] = fp16(s*u) (hi) and Ap[lo_row + j] = fp16(s*u - hi) (lo),
@@ -316,7 +337,7 @@ pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long 
     __shared__ float t[32][33];
     const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    const float sc = SPLIT == 2 ? *scale : 1.0f;
+    const float sc = (SPLIT == 2 || sizeof(H) == 1) ? *scale : 1.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int k = k0 + ty + 8 * q, j = j0 + tx;
@@ -341,7 +362,7 @@ template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
 pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, H *__restrict__ Bp, long lo_row,
                  const float *__restrict__ scale) {
-    const float sc = SPLIT == 2 ? *scale : 1.0f;
+    const float sc = (SPLIT == 2 || sizeof(H) == 1) ? *scale : 1.0f;
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M; i += gridDim.x * (blockDim.x >> 5)) {
         const float *src = L + (long)i * ldl;
@@ -379,18 +400,19 @@ absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigne
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// Power-of-two scales: sU = 2^(14 - ceil(log2 max|U|)) and sL = 2^13 when
-// |l| <= 1 (partial pivoting), else sL from max|L| (umax_bits[1]) like sU;
-// writes sL, sU and 1 / (sL sU).
-__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales, int l_from_max) {
-    auto scale_exp = [](unsigned bits) {
+// Power-of-two scales: sU = 2^(top - ceil(log2 max|U|)) and sL = 2^(top - 1)
+// when |l| <= 1 (partial pivoting), else sL from max|L| (umax_bits[1]) like
+// sU; top = 14 for the split fp16 operands (below 65504), 8 for E4M3 (below
+// 448); writes sL, sU and 1 / (sL sU).
+__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales, int l_from_max, int top) {
+    auto scale_exp = [top](unsigned bits) {
         const float m = __uint_as_float(bits);
         int e = 0;
         if (m > 0.f && m < INFINITY) frexpf(m, &e);  // m < 2^e
-        return 14 - e;
+        return top - e;
     };
     const int eu = scale_exp(umax_bits[0]);
-    const int el = l_from_max ? scale_exp(umax_bits[1]) : 13;
+    const int el = l_from_max ? scale_exp(umax_bits[1]) : top - 1;
     scales[0] = ldexpf(1.0f, el);
     scales[1] = ldexpf(1.0f, eu);
     scales[2] = ldexpf(1.0f, -el - eu);
@@ -413,15 +435,20 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-// 2-D map over a (rows x kpad) K-major 16-bit array, box (64 x box_rows), 128B swizzle.
-cudaError_t make_map(CUtensorMap *m, const void *base, long rows, int kpad, int box_rows, bool bf16) {
+// 2-D map over a (rows x kpad) K-major array of fmt (0 fp16, 1 bf16, 2 E4M3
+// bytes), box (128 bytes of K x box_rows), 128B swizzle.
+cudaError_t make_map(CUtensorMap *m, const void *base, long rows, int kpad, int box_rows, int fmt) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
+    const int esz = fmt == 2 ? 1 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+    const CUtensorMapDataType dt = fmt == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = enc(m, dt, 2,
                      const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -446,15 +473,15 @@ struct TcWs {
 };
 
 // Scratch layout: [Ap: rowsA x Kpad][Bp: rowsB x Kpad][umax, scales]
-TcWs carve_ws(void *ws, int M, int N, int Kpad, int split) {
+TcWs carve_ws(void *ws, int M, int N, int Kpad, int split, int esz) {
     const long rowsA = split == 2 ? 2L * ((N + TILE_J - 1) / TILE_J * TILE_J) : N;
     const long rowsB = split == 2 ? 2L * ((M + TILE_I - 1) / TILE_I * TILE_I) : M;
     char *p = static_cast<char *>(ws);
     TcWs w;
     w.Ap = p;
-    p += align_up((size_t)rowsA * Kpad * 2, 1024);
+    p += align_up((size_t)rowsA * Kpad * esz, 1024);
     w.Bp = p;
-    p += align_up((size_t)rowsB * Kpad * 2, 1024);
+    p += align_up((size_t)rowsB * Kpad * esz, 1024);
     w.umax = reinterpret_cast<unsigned *>(p);
     w.scales = reinterpret_cast<float *>(p + 16);
     return w;
@@ -466,19 +493,24 @@ TcWs carve_ws(void *ws, int M, int N, int Kpad, int split) {
 template <typename H, uint32_t FMT, int SPLIT>
 cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22, long lda,
                 void *ws, MpDevStatus *st, cudaStream_t s, bool nt = false, int lower = 0) {
-    const int Kpad = (K + BK - 1) / BK * BK;
-    TcWs w = carve_ws(ws, M, N, Kpad, SPLIT);
+    constexpr int BKE = bk_elems<FMT>();
+    constexpr bool SCALED = scaled<FMT, SPLIT>();
+    const int Kpad = (K + BKE - 1) / BKE * BKE;
+    TcWs w = carve_ws(ws, M, N, Kpad, SPLIT, (int)sizeof(H));
+    const bool lmax = nt || FMT == 2;  // L's scale from its magnitude too
     H *Ap = reinterpret_cast<H *>(w.Ap);
     H *Bp = reinterpret_cast<H *>(w.Bp);
     const long a_lo = SPLIT == 2 ? (long)(N + TILE_J - 1) / TILE_J * TILE_J : 0;
     const long b_lo = SPLIT == 2 ? (long)(M + TILE_I - 1) / TILE_I * TILE_I : 0;
     cudaError_t e;
-    if (SPLIT == 2) {
-        // padding rows of the hi halves must be zero
-        e = cudaMemsetAsync(Ap, 0, (size_t)2 * a_lo * Kpad * sizeof(H), s);
-        if (e != cudaSuccess) return e;
-        e = cudaMemsetAsync(Bp, 0, (size_t)2 * b_lo * Kpad * sizeof(H), s);
-        if (e != cudaSuccess) return e;
+    if (SCALED) {
+        if (SPLIT == 2) {
+            // padding rows of the hi halves must be zero
+            e = cudaMemsetAsync(Ap, 0, (size_t)2 * a_lo * Kpad * sizeof(H), s);
+            if (e != cudaSuccess) return e;
+            e = cudaMemsetAsync(Bp, 0, (size_t)2 * b_lo * Kpad * sizeof(H), s);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaMemsetAsync(w.umax, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         mp_note_launch();
@@ -486,12 +518,12 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
             absmax_kernel<<<1216, 256, 0, s>>>(N, K, U12, ldu, w.umax);
         else
             absmax_kernel<<<1216, 256, 0, s>>>(K, N, U12, ldu, w.umax);
-        if (nt) {
+        if (lmax) {
             mp_note_launch();
             absmax_kernel<<<1216, 256, 0, s>>>(M, K, L21, ldl, w.umax + 1);
         }
         mp_note_launch();
-        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales, nt ? 1 : 0);
+        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales, lmax ? 1 : 0, FMT == 2 ? 8 : 14);
     }
     {
         if (nt) {
@@ -512,9 +544,9 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
         if (e != cudaSuccess) return e;
     }
     CUtensorMap mapA, mapB;
-    e = make_map(&mapA, Ap, SPLIT == 2 ? 2 * a_lo : N, Kpad, TILE_J, FMT == 1);
+    e = make_map(&mapA, Ap, SPLIT == 2 ? 2 * a_lo : N, Kpad, TILE_J, (int)FMT);
     if (e != cudaSuccess) return e;
-    e = make_map(&mapB, Bp, SPLIT == 2 ? 2 * b_lo : M, Kpad, TILE_I, FMT == 1);
+    e = make_map(&mapB, Bp, SPLIT == 2 ? 2 * b_lo : M, Kpad, TILE_I, (int)FMT);
     if (e != cudaSuccess) return e;
     auto kern = tc_update_kernel<FMT, SPLIT>;
     constexpr size_t smem = smem_bytes<SPLIT>();
@@ -523,7 +555,7 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     const int ntiles = ((M + TILE_I - 1) / TILE_I) * ((N + TILE_J - 1) / TILE_J);
     const int grid = std::min(ntiles, num_sms());
     mp_note_launch();
-    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BK, (int)a_lo, (int)b_lo,
+    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BKE, (int)a_lo, (int)b_lo,
                                          w.scales + 2, st, lower);
     return cudaGetLastError();
 }
@@ -531,7 +563,8 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
 }  // namespace
 
 size_t tc_workspace_bytes(int n, int nb, int prec) {
-    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3) return 0;
+    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3 && prec != MP_PREC_E4M3) return 0;
+    // 2-byte elements with K padded to 64 bound the E4M3 case (1 byte, K padded to 128)
     const size_t kpad = (size_t)(nb + BK - 1) / BK * BK;
     const int split = prec == MP_PREC_FP16X3 ? 2 : 1;
     const size_t rowsA = split == 2 ? 2 * ((size_t)(n + TILE_J - 1) / TILE_J * TILE_J) : (size_t)n;
@@ -545,6 +578,7 @@ cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, 
     if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    if (prec == MP_PREC_E4M3) return run<__nv_fp8_e4m3, 2, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
     return cudaErrorInvalidValue;
 }
 
@@ -554,5 +588,7 @@ cudaError_t tc_update_nt(int prec, int M, int N, int K, const float *A, long lda
     if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
     if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
     if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
+    if (prec == MP_PREC_E4M3)
+        return run<__nv_fp8_e4m3, 2, 1>(M, N, K, A, lda, B, ldb, C, ldc, ws, st, s, true, lower);
     return cudaErrorInvalidValue;
 }
