@@ -115,6 +115,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest rank's time); the
+    value itself when running alone."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(work_per_rank, world, ms_max):
+    """Throughput of the whole job: every rank's work (replicas: the same
+    amount each) divided by the slowest rank's time, in units of 1e9/s."""
+    return work_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
 def cpu_oracle_rate(n, seed=0, reps=1):
     """Times the CPU oracle (Algorithm 1, FP32 factor, FP64 refinement) on n."""
     import oracle
@@ -251,8 +268,8 @@ def main():
                          "workloads (SPD Cholesky, batched small systems, adjoint solve)")
     ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
     ap.add_argument("--nb", type=int, default=0)
-    ap.add_argument("--ref-n", type=int, default=2048)
-    ap.add_argument("--cpu-n", type=int, default=3072)
+    ap.add_argument("--ref-n", type=int, default=4096)
+    ap.add_argument("--cpu-n", type=int, default=8192)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -320,13 +337,9 @@ def main():
     clk = clocks.stop()
     prof = solver.profile_collect()
     solver.profile_enable(())
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda")
     flops = 2.0 * n ** 3 / 3.0
-    value = flops * ws / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(flops, ws, ms_step)
 
     # correctness of the timed solves (library's own FP64 residual, and a check
     # of the final X through the residual entry point)
@@ -387,12 +400,8 @@ def main():
             host_solve()
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": flops * ws / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist, "cuda")
+        e2e = {"value": whole_job_rate(flops, ws, e2e_ms), "unit": "GFLOP/s",
                "h2d_bytes_per_step": 8 * n * n + 8 * n * nrhs,
                "d2h_bytes_per_step": 8 * n * nrhs + 4 * n, "ms_per_step": e2e_ms}
         del wh

@@ -1,0 +1,67 @@
+"""Parity at the full sizes of the measured workloads, in the configuration
+the benchmark times (default options: the fp16x3 rung, classical
+refinement).  The oracle checks what it can afford at these sizes: the
+backward error of every column from its compensated (Dot2) FP64 residual over
+the whole matrix, and, where the condition number is known in closed form,
+the forward error.
+"""
+import numpy as np
+import pytest
+
+from paper_0808_2794_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    return t
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_0808_2794_gb300 import solver
+    solver.load()
+    return solver
+
+
+def test_dense_lu_n16384_bench_configuration(torch, mp, orc):
+    """The benchmark's workload: n = 16384, A ~ N(0,1), x ~ U[-1,1], b = A x."""
+    n = 16384
+    A, B, X_true = inputs.dense_system(n, seed=0)
+    X, piv, st = mp.gesv(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+    assert st["flags"] == 0 and st["iter"] >= 1, st
+    X = X.cpu().numpy().reshape(n, 1)
+    assert np.all(orc.bwd_err(A, X, B) <= 1e-14)
+    p = piv.cpu().numpy()
+    assert np.all((p >= np.arange(1, n + 1)) & (p <= n))  # LAPACK ipiv: row k swapped with ipiv[k] >= k
+    # the solution agrees with x_true to well inside the FP32-factor regime
+    assert np.max(np.abs(X[:, 0] - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-9
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e8])
+def test_spd_n4096_fp16_prescribed_kappa(torch, mp, orc, kappa):
+    """SPD systems of prescribed condition number (the paper's Fig. 4
+    protocol), n = 4096, nrhs = 4, FP16 Cholesky with automatic GMRES
+    continuation and FP64 fallback: every column reaches bwd <= 1e-14 and the
+    forward error is within 20 kappa_inf u64 of X_true (kappa_inf from the
+    closed-form inverse U diag(1/s) U^T)."""
+    n, nrhs = 4096, 4
+    A, B, X_true = inputs.conditioned_system(n, kappa, nrhs=nrhs, spd=True, seed=0)
+    X, st = mp.posv(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), prec="fp16", refine="auto")
+    X = X.cpu().numpy()
+    assert np.all(orc.bwd_err(A, X, B) <= 1e-14), st
+    # closed-form inverse: A = U diag(s) U^T with the generator's U and s
+    rng = np.random.default_rng(0)
+    U = inputs.haar_orthogonal(rng, n)
+    s = kappa ** (-np.arange(n, dtype=np.float64) / (n - 1))
+    Ainv = (U / s[None, :]) @ U.T
+    kinf = np.max(np.sum(np.abs(A), axis=1)) * np.max(np.sum(np.abs(Ainv), axis=1))
+    fwd = np.max(np.abs(X - X_true)) / np.max(np.abs(X_true))
+    assert fwd <= 20 * kinf * U64, (fwd, kinf, st)
+    if kappa <= 1e4:
+        assert not st["flags"] & mp.FLAG_FALLBACK, st
