@@ -3,6 +3,7 @@
 // blocks; Section 2.1: PA = LU).  All matrices are row-major.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -117,136 +118,287 @@ apply_moves_kernel(T *__restrict__ W, long ld, const int2 *__restrict__ pairs,
 }
 
 // One leaf step of the panel factorization, after the leaf (columns
-// [k, k+kb)) has been factored and its rows exchanged:
+// [k, k+kb)) has been factored:
 //   U = X A12, X = L11^{-1} from the panel kernel
-//                     (A12: rows k..k+kb of the columns [k+kb, k+kb+N))
+//                     (A12: rows k..k+kb of the columns [k+kb+coff, k+kb+coff+N))
 //   A22 -= L21 U      (rows [k+kb, k+kb+M) of the same columns)
-// in one launch over (64-row tile, 128-column chunk) pairs.  Columns of U
-// are independent, so every CTA forms the U columns of its chunk in shared
-// memory (the same arithmetic in each CTA of a chunk, so all copies agree
-// bit for bit) and updates its 64 x 128 tile of A22 with FP32 (FP64)
-// FMAs in the order l = 0..kb-1.  The CTA that draws the last ticket of a
-// chunk, i.e. after every CTA of that chunk has read its A12 columns, writes
-// them back as U and resets the ticket.  No CTA waits for another.
-constexpr int kLeafTileRows = 64;
+// over (TR-row tile, 128-column chunk) pairs.  Columns of U are independent,
+// so every tile forms the U columns of its chunk in shared memory (the same
+// arithmetic in each, so all copies agree bit for bit) and updates its
+// TR x 128 tile of A22 with FP32 (FP64) FMAs in the order l = 0..kb-1.
+//
+// Two forms.  (a) After the leaf's row exchange: one CTA per tile.  (b)
+// Persistent, with the exchange folded in: A12 rows are read from the rows
+// the moves bring there, tiles skip the moved rows of A22, and the tile that
+// draws the last ticket of its chunk computes the moved rows (source row -
+// L21 U) into shared memory and stores them.  Every write that another tile
+// of the chunk could still read (U over A12, the moved rows) is made by that
+// last tile, after every tile of the chunk has finished reading.  No CTA waits
+// for another.
 constexpr int kLeafTileCols = 128;
+// dynamic shared memory of the persistent form: a staging area (moved rows,
+// exchange tiles) and a bitmap of the moved rows of A22; more than half of an
+// SM's shared memory, so that it runs at one CTA per SM
+constexpr int kLeafStageBytes = 24 * 1024;
+inline size_t leaf_update_pad_bytes() { return 120 * 1024; }
+constexpr int kLeafMaxBitmapRows = (120 - 24) * 1024 * 8;
 
-template <typename T, int KBMAX>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-leaf_update_kernel(T *W, long ld, int k, int kb, int N, int M, const T *__restrict__ X, int xs,
-                   unsigned *tickets) {
-    __shared__ __align__(16) T Us[KBMAX][kLeafTileCols];
-    __shared__ T Ls[KBMAX][KBMAX + 1];  // X = L11^{-1} (unit lower)
-    __shared__ T Lt[kLeafTileRows][KBMAX + 1];
-    __shared__ bool last;
+template <typename T, int KBMAX, int TR>
+struct LeafSmem {
+    __align__(16) T Us[KBMAX][kLeafTileCols];
+    T Ls[KBMAX][KBMAX + 1];  // X = L11^{-1} (unit lower)
+    T Lt[TR][KBMAX + 1];
+    int a12[KBMAX];          // row that A12 row i is read from
+    int2 mv[2 * KBMAX];      // moved rows of A22: (destination, source)
+    int nmv;
+    bool last;
+};
+
+// One (TR-row tile, chunk) of the leaf step; R = row tiles per chunk.
+// MOVES: the persistent form (b), with bits = moved rows of A22 (bit r: row
+// k+kb+r) and stage = kLeafStageBytes of shared memory.
+template <typename T, int KBMAX, int TR, bool MOVES>
+__device__ __forceinline__ void leaf_tile(LeafSmem<T, KBMAX, TR> &sm, T *W, long ld, int k, int kb, int coff, int N,
+                                          int M, unsigned *tickets, int r0, int chunk, int R, const unsigned *bits,
+                                          T *stage) {
+    constexpr int NTHR = TR * 4, NG = NTHR / kLeafTileCols;
     const int tid = threadIdx.x;
-    const int r0 = blockIdx.x * kLeafTileRows;
-    const int chunk = blockIdx.y, c0 = chunk * kLeafTileCols;
+    const int c0 = chunk * kLeafTileCols;
     const int w = min(kLeafTileCols, N - c0);
-    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        const int i = idx / kb, l = idx - i * kb;
-        Ls[i][l] = l < i ? X[i * xs + l] : T(0);
-    }
-    for (int idx = tid; idx < kb * kLeafTileCols; idx += blockDim.x) {
+    const int cb = k + kb + coff + c0;  // first column of the chunk
+    for (int idx = tid; idx < kb * kLeafTileCols; idx += NTHR) {
         const int i = idx / kLeafTileCols, c = idx - i * kLeafTileCols;
-        Us[i][c] = c < w ? W[(long)(k + i) * ld + k + kb + c0 + c] : T(0);
+        const int row = MOVES ? sm.a12[i] : k + i;
+        sm.Us[i][c] = c < w ? W[(long)row * ld + cb + c] : T(0);
     }
-    for (int idx = tid; idx < kLeafTileRows * kb; idx += blockDim.x) {
+    for (int idx = tid; idx < TR * kb; idx += NTHR) {
         const int r = idx / kb, l = idx - r * kb;
-        Lt[r][l] = r0 + r < M ? W[(long)(k + kb + r0 + r) * ld + k + l] : T(0);
+        sm.Lt[r][l] = r0 + r < M ? W[(long)(k + kb + r0 + r) * ld + k + l] : T(0);
     }
     __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        last = atomicAdd(&tickets[chunk], 1u) == gridDim.x - 1;
-    }
-    // U = X A12 for the chunk's columns: thread (g, c) forms rows g, g+2, ...
+    // U = X A12 for the chunk's columns: thread (g, c) forms rows g, g+NG, ...
     // of column c (independent dot products, l in order)
     {
-        const int c = tid & (kLeafTileCols - 1), g = tid >> 7;
-        T u[(KBMAX + 1) / 2];
+        const int c = tid & (kLeafTileCols - 1), g = tid / kLeafTileCols;
+        T u[(KBMAX + NG - 1) / NG];
 #pragma unroll
-        for (int q = 0; q < (KBMAX + 1) / 2; ++q) {
-            const int i = g + 2 * q;
-            T v = i < kb ? Us[i][c] : T(0);
-            for (int l = 0; l < i; ++l) v = fma(Ls[i][l], Us[l][c], v);
+        for (int q = 0; q < (KBMAX + NG - 1) / NG; ++q) {
+            const int i = g + NG * q;
+            T v = i < kb ? sm.Us[i][c] : T(0);
+            for (int l = 0; l < i; ++l) v = fma(sm.Ls[i][l], sm.Us[l][c], v);
             u[q] = v;
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < (KBMAX + 1) / 2; ++q) {
-            const int i = g + 2 * q;
-            if (i < kb) Us[i][c] = u[q];
+        for (int q = 0; q < (KBMAX + NG - 1) / NG; ++q) {
+            const int i = g + NG * q;
+            if (i < kb) sm.Us[i][c] = u[q];
         }
     }
     __syncthreads();
-    if (last) {
-        for (int idx = tid; idx < kb * kLeafTileCols; idx += blockDim.x) {
-            const int i = idx / kLeafTileCols, c = idx - i * kLeafTileCols;
-            if (c < w) W[(long)(k + i) * ld + k + kb + c0 + c] = Us[i][c];
-        }
-        if (tid == 0) tickets[chunk] = 0u;
-    }
-    // this thread's 8 rows x 4 columns of the A22 tile (16-byte
-    // vectors when the 4 columns are inside the tile: the tile starts on a
-    // multiple of 4 columns and ld is a multiple of 32)
+    // this thread's 8 rows x 4 columns of the A22 tile (16-byte vectors when
+    // the 4 columns are inside the tile: the tile starts on a multiple of 4
+    // columns and ld is a multiple of 32)
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     constexpr int VW = 16 / sizeof(T);
-    const int ty = tid >> 5, tx = tid & 31;
-    const bool full4 = tx * 4 + 3 < w;
-    T acc[8][4];
+    {
+        const int ty = tid >> 5, tx = tid & 31;
+        const bool full4 = tx * 4 + 3 < w;
+        const int rows = M - (r0 + ty * 8);  // rows of this thread's 8 inside A22
+        T *const tile = W + (long)(k + kb + r0 + ty * 8) * ld + (cb + tx * 4);
+        T acc[8][4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int r = r0 + ty * 8 + a;
-        const T *src = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
-        if (r < M && full4) {
+        for (int a = 0; a < 8; ++a) {
+            const T *src = tile + (long)a * ld;
+            if (a < rows && full4) {
+#pragma unroll
+                for (int q = 0; q < 4 / VW; ++q) {
+                    const V v = reinterpret_cast<const V *>(src)[q];
+                    const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = (a < rows && tx * 4 + b < w) ? src[b] : T(0);
+            }
+        }
+        for (int l = 0; l < kb; ++l) {
+            T bv[4], av[8];
 #pragma unroll
             for (int q = 0; q < 4 / VW; ++q) {
-                const V v = reinterpret_cast<const V *>(src)[q];
+                const V v = reinterpret_cast<const V *>(&sm.Us[l][tx * 4])[q];
                 const T *pv = reinterpret_cast<const T *>(&v);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
+                for (int e = 0; e < VW; ++e) bv[q * VW + e] = pv[e];
             }
-        } else {
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = (r < M && tx * 4 + b < w) ? src[b] : T(0);
+            for (int a = 0; a < 8; ++a) av[a] = sm.Lt[ty * 8 + a][l];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            if (a >= rows) continue;
+            if (MOVES) {
+                const int rr = r0 + ty * 8 + a;
+                if ((bits[rr >> 5] >> (rr & 31)) & 1u) continue;  // a moved row: the last tile stores it
+            }
+            T *dst = tile + (long)a * ld;
+            if (full4) {
+#pragma unroll
+                for (int q = 0; q < 4 / VW; ++q) {
+                    V v;
+                    T *pv = reinterpret_cast<T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) pv[e] = acc[a][q * VW + e];
+                    reinterpret_cast<V *>(dst)[q] = v;
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (tx * 4 + b < w) dst[b] = acc[a][b];
+            }
         }
     }
-    for (int l = 0; l < kb; ++l) {
-        T bv[4], av[8];
-#pragma unroll
-        for (int q = 0; q < 4 / VW; ++q) {
-            const V v = reinterpret_cast<const V *>(&Us[l][tx * 4])[q];
-            const T *pv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) bv[q * VW + e] = pv[e];
+    // every read of A12 (and of the moved rows' sources) in this tile is done
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sm.last = atomicAdd(&tickets[chunk], 1u) == (unsigned)R - 1;
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+    if (MOVES) {  // moved rows d of A22: W[src] - L21[d] U, staged before any store
+        for (int idx = tid; idx < sm.nmv * kLeafTileCols; idx += NTHR) {
+            const int j = idx / kLeafTileCols, c = idx - j * kLeafTileCols;
+            if (c >= w) continue;
+            const int2 mv = sm.mv[j];
+            T v = W[(long)mv.y * ld + cb + c];
+            const T *lrow = W + (long)mv.x * ld + k;
+            for (int l = 0; l < kb; ++l) v = fma(-lrow[l], sm.Us[l][c], v);
+            stage[idx] = v;
         }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) av[a] = Lt[ty * 8 + a][l];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+        __syncthreads();
     }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int r = r0 + ty * 8 + a;
-        if (r >= M) continue;
-        T *dst = W + (long)(k + kb + r) * ld + k + kb + c0 + tx * 4;
-        if (full4) {
-#pragma unroll
-            for (int q = 0; q < 4 / VW; ++q) {
-                V v;
-                T *pv = reinterpret_cast<T *>(&v);
-#pragma unroll
-                for (int e = 0; e < VW; ++e) pv[e] = acc[a][q * VW + e];
-                reinterpret_cast<V *>(dst)[q] = v;
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (tx * 4 + b < w) dst[b] = acc[a][b];
+    for (int idx = tid; idx < kb * kLeafTileCols; idx += NTHR) {
+        const int i = idx / kLeafTileCols, c = idx - i * kLeafTileCols;
+        if (c < w) W[(long)(k + i) * ld + cb + c] = sm.Us[i][c];
+    }
+    if (MOVES)
+        for (int idx = tid; idx < sm.nmv * kLeafTileCols; idx += NTHR) {
+            const int j = idx / kLeafTileCols, c = idx - j * kLeafTileCols;
+            if (c < w) W[(long)sm.mv[j].x * ld + cb + c] = stage[idx];
         }
+    if (tid == 0) tickets[chunk] = 0u;
+}
+
+template <typename T, int KBMAX, int TR>
+__device__ __forceinline__ void leaf_load_x(LeafSmem<T, KBMAX, TR> &sm, int kb, const T *__restrict__ X, int xs) {
+    for (int idx = threadIdx.x; idx < kb * kb; idx += TR * 4) {
+        const int i = idx / kb, l = idx - i * kb;
+        sm.Ls[i][l] = l < i ? X[i * xs + l] : T(0);
+    }
+}
+
+// Form (a): one CTA per tile, grid (row tiles, chunks).
+template <typename T, int KBMAX>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+leaf_update_kernel(T *W, long ld, int k, int kb, int coff, int N, int M, const T *__restrict__ X, int xs,
+                   unsigned *tickets) {
+    __shared__ LeafSmem<T, KBMAX, 64> sm;
+    leaf_load_x(sm, kb, X, xs);
+    leaf_tile<T, KBMAX, 64, false>(sm, W, ld, k, kb, coff, N, M, tickets, blockIdx.x * 64, blockIdx.y, gridDim.x,
+                                   nullptr, nullptr);
+}
+
+// Form (b): persistent, 128-row tiles; CTA b takes work items b, b +
+// gridDim.x, ...: first the update tiles (chunk-major, so consecutive CTAs
+// share a chunk's A12 columns in L2), then the leaf's row exchange over the
+// column ranges [0, mc1) and [mc2, mc3) (the columns outside the outer panel)
+// in chunks of kMoveBytes, then the running row permutation perm.  An
+// exchange item reads every source row of its chunk into shared memory
+// before it writes any destination row, as the moves form cycles.
+constexpr int kMoveBytes = 512;
+
+template <typename T, int KBMAX>
+__global__ void __launch_bounds__(512, 1)
+leaf_update_persistent_kernel(T *W, long ld, int k, int kb, int coff, int N, int M, const T *__restrict__ X, int xs,
+                              unsigned *tickets, const int2 *__restrict__ pairs, const int *__restrict__ npairs,
+                              int mc1, int mc2, int mc3, int *perm) {
+    __shared__ LeafSmem<T, KBMAX, 128> sm;
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    T *stage = reinterpret_cast<T *>(dyn_raw);
+    unsigned *bits = reinterpret_cast<unsigned *>(dyn_raw + kLeafStageBytes);
+    constexpr int CWm = kMoveBytes / sizeof(T);
+    const int tid = threadIdx.x;
+    const int R = max(1, (M + 127) / 128), C = N > 0 ? (N + kLeafTileCols - 1) / kLeafTileCols : 0;
+    const int n1 = (mc1 + CWm - 1) / CWm, n2 = mc3 > mc2 ? (mc3 - mc2 + CWm - 1) / CWm : 0;
+    const int nitems = R * C + n1 + n2 + (perm ? 1 : 0);
+    if ((int)blockIdx.x >= nitems) return;
+    const int np = min(*npairs, 2 * KBMAX);
+    // the moves: A12 sources, the moved rows of A22 (list and bitmap)
+    leaf_load_x(sm, kb, X, xs);
+    if (tid < kb) sm.a12[tid] = k + tid;
+    if (tid == 0) sm.nmv = 0;
+    const int words = (M + 31) / 32;
+    for (int i = tid; i < words; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    for (int t = tid; t < np; t += blockDim.x) {
+        const int2 mv = pairs[t];
+        if (mv.x < k + kb) {
+            sm.a12[mv.x - k] = mv.y;
+        } else if (mv.x - (k + kb) < M) {
+            sm.mv[atomicAdd(&sm.nmv, 1)] = mv;
+            const int rr = mv.x - (k + kb);
+            atomicOr(&bits[rr >> 5], 1u << (rr & 31));
+        }
+    }
+    __syncthreads();
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        if (t < R * C) {
+            const int chunk = t / R;
+            leaf_tile<T, KBMAX, 128, true>(sm, W, ld, k, kb, coff, N, M, tickets, (t - chunk * R) * 128, chunk, R,
+                                           bits, stage);
+        } else if (t < R * C + n1 + n2) {
+            const int q = t - R * C;
+            const int cs = q < n1 ? q * CWm : mc2 + (q - n1) * CWm;
+            const int ce = q < n1 ? min(cs + CWm, mc1) : min(cs + CWm, mc3);
+            using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            constexpr int VW = 16 / sizeof(T), NV = CWm / VW;
+            V *tile = reinterpret_cast<V *>(stage);
+            // cs is a multiple of CWm and ld of 32, so a vector is either
+            // wholly inside [cs, ce) or (at the ragged end) read by elements
+            for (int idx = tid; idx < np * NV; idx += blockDim.x) {
+                const int pr = idx / NV, c = cs + (idx - pr * NV) * VW;
+                const T *src = W + (long)pairs[pr].y * ld + c;
+                if (c + VW <= ce) {
+                    tile[idx] = *reinterpret_cast<const V *>(src);
+                } else {
+                    T *pv = reinterpret_cast<T *>(&tile[idx]);
+                    for (int e = 0; e < VW; ++e) pv[e] = c + e < ce ? src[e] : T(0);
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < np * NV; idx += blockDim.x) {
+                const int pr = idx / NV, c = cs + (idx - pr * NV) * VW;
+                T *dst = W + (long)pairs[pr].x * ld + c;
+                if (c + VW <= ce) {
+                    *reinterpret_cast<V *>(dst) = tile[idx];
+                } else {
+                    const T *pv = reinterpret_cast<const T *>(&tile[idx]);
+                    for (int e = 0; e < VW; ++e)
+                        if (c + e < ce) dst[e] = pv[e];
+                }
+            }
+        } else {  // the running row permutation
+            int *pv = reinterpret_cast<int *>(stage);
+            for (int i = tid; i < np; i += blockDim.x) pv[i] = perm[pairs[i].y];
+            __syncthreads();
+            for (int i = tid; i < np; i += blockDim.x) perm[pairs[i].x] = pv[i];
+        }
+        __syncthreads();  // the shared arrays are reused by the next item
     }
 }
 
@@ -275,20 +427,102 @@ cudaError_t launch_compose_swaps(const int32_t *ipiv, int k1, int k2, int n, int
 }
 
 template <typename T>
-cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int N, int M, const T *X, int xs, unsigned *tickets,
-                               cudaStream_t s) {
+cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
+                               unsigned *tickets, cudaStream_t s) {
     constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
     if (N <= 0 || kb <= 0 || M < 0) return cudaSuccess;
     if (kb > KBMAX || N > 1024) return cudaErrorInvalidValue;
-    dim3 grid(std::max(1, (M + kLeafTileRows - 1) / kLeafTileRows), (N + kLeafTileCols - 1) / kLeafTileCols);
+    dim3 grid(std::max(1, (M + 63) / 64), (N + kLeafTileCols - 1) / kLeafTileCols);
     mp_note_launch();
-    leaf_update_kernel<T, KBMAX><<<grid, 256, 0, s>>>(W, ld, k, kb, N, M, X, xs, tickets);
+    leaf_update_kernel<T, KBMAX><<<grid, 256, 0, s>>>(W, ld, k, kb, coff, N, M, X, xs, tickets);
     return cudaGetLastError();
 }
-template cudaError_t launch_leaf_update<float>(float *, long, int, int, int, int, const float *, int, unsigned *,
-                                              cudaStream_t);
-template cudaError_t launch_leaf_update<double>(double *, long, int, int, int, int, const double *, int, unsigned *,
-                                               cudaStream_t);
+template cudaError_t launch_leaf_update<float>(float *, long, int, int, int, int, int, const float *, int,
+                                              unsigned *, cudaStream_t);
+template cudaError_t launch_leaf_update<double>(double *, long, int, int, int, int, int, const double *, int,
+                                               unsigned *, cudaStream_t);
+
+namespace {
+template <typename T>
+void leaf_rest_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int clusters, int cluster,
+                      cudaStream_t s) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(clusters * cluster, 1, 1);
+    cfg.blockDim = dim3(512, 1, 1);
+    cfg.dynamicSmemBytes = leaf_update_pad_bytes();
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+template <typename T>
+cudaError_t leaf_rest_attrs() {
+    constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
+    auto kern = leaf_update_persistent_kernel<T, KBMAX>;
+    cudaError_t e = mp_smem_attr(kern, leaf_update_pad_bytes());
+    if (e != cudaSuccess) return e;
+    return mp_func_attr_once(reinterpret_cast<const void *>(kern), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_leaf_rest(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
+                             unsigned *tickets, const int2 *pairs, const int *npairs, int mc1, int mc2, int mc3,
+                             int *perm, int clusters, int cluster, cudaStream_t s) {
+    constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
+    static_assert(2 * KBMAX * kMoveBytes <= kLeafStageBytes, "exchange tile exceeds the staging area");
+    static_assert(2 * KBMAX * kLeafTileCols * (int)sizeof(T) <= kLeafStageBytes, "moved rows exceed the staging area");
+    if (kb <= 0 || M < 0 || N < 0 || clusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
+    if (kb > KBMAX || N > 1024 || mc1 < 0 || mc3 < mc2 || M > kLeafMaxBitmapRows) return cudaErrorInvalidValue;
+    cudaError_t e = leaf_rest_attrs<T>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    leaf_rest_config<T>(cfg, attr, clusters, cluster, s);
+    mp_note_launch();
+    return cudaLaunchKernelEx(&cfg, leaf_update_persistent_kernel<T, KBMAX>, W, ld, k, kb, coff, N, M, X, xs,
+                              tickets, pairs, npairs, mc1, mc2, mc3, perm);
+}
+template cudaError_t launch_leaf_rest<float>(float *, long, int, int, int, int, int, const float *, int, unsigned *,
+                                            const int2 *, const int *, int, int, int, int *, int, int, cudaStream_t);
+template cudaError_t launch_leaf_rest<double>(double *, long, int, int, int, int, int, const double *, int,
+                                             unsigned *, const int2 *, const int *, int, int, int, int *, int, int,
+                                             cudaStream_t);
+
+// Clusters of `cluster` CTAs of the persistent leaf update (one CTA per SM)
+// that fit on the device at once, minus one: the remaining slot is left for
+// the panel kernel of the same cluster size.  0 when no such split exists.
+template <typename T>
+int leaf_update_rest_clusters(int cluster) {
+    static std::mutex mu;
+    static int cache[2][64][17];
+    static bool have[2][64][17];
+    int dev = 0;
+    if (cluster < 1 || cluster > 16 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const int ti = sizeof(T) == 4 ? 0 : 1;
+    std::lock_guard<std::mutex> g(mu);
+    if (!have[ti][dev][cluster]) {
+        constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
+        int nc = 0;
+        if (leaf_rest_attrs<T>() == cudaSuccess) {
+            cudaLaunchConfig_t cfg;
+            cudaLaunchAttribute attr[1];
+            leaf_rest_config<T>(cfg, attr, 1, cluster, nullptr);
+            if (cudaOccupancyMaxActiveClusters(
+                    &nc, reinterpret_cast<const void *>(leaf_update_persistent_kernel<T, KBMAX>), &cfg) != cudaSuccess)
+                nc = 0;
+        }
+        cudaGetLastError();
+        cache[ti][dev][cluster] = std::max(0, nc - 1);
+        have[ti][dev][cluster] = true;
+    }
+    return cache[ti][dev][cluster];
+}
+template int leaf_update_rest_clusters<float>(int);
+template int leaf_update_rest_clusters<double>(int);
 
 template <typename T>
 cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npairs, int max_pairs,

@@ -7,6 +7,8 @@
 
 // ---- pivoted panel (panel.cu) ----------------------------------------------
 template <typename T> int panel_base_width(int m);
+// CTAs in the cluster of the panel kernel for a panel of height m.
+template <typename T> int panel_cluster_size(int m);
 // LU with partial pivoting of the m x ncols panel starting at P (row-major, ld),
 // ncols <= panel_base_width<T>(m).  ipiv[j] (j < ncols) receives the global
 // 1-based pivot row row0 + p + 1; moves[0 .. *nmoves) receives the composed
@@ -14,9 +16,23 @@ template <typename T> int panel_base_width(int m);
 // (global row indices, at most 2 * ncols).  linv (optional): receives the
 // inverse of the unit-lower ncols x ncols L11, row-major with stride
 // panel_base_width<T>(m).
+//
+// prev (optional, prev.kb > 0): the previous leaf of the same outer panel,
+// whose row moves and update the panel's columns have NOT received yet; the
+// kernel applies them while loading (rows taken through the moves, then
+// A -= L21 U with U = X A12, the same FMA order as launch_leaf_update) and
+// writes U to the previous leaf's rows (prev.kb rows above P).
+template <typename T>
+struct PanelPrev {
+    const T *X = nullptr;          // the previous leaf's L11^{-1}, row-major, stride xs
+    const int2 *pairs = nullptr;   // its row moves (destination, source), global rows
+    const int *npairs = nullptr;   // their count (device)
+    int xs = 0;
+    int kb = 0;                    // its width; its columns end where the panel starts
+};
 template <typename T>
 cudaError_t launch_panel(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                         int *nmoves, MpDevStatus *st, T *linv, cudaStream_t s);
+                         int *nmoves, MpDevStatus *st, T *linv, PanelPrev<T> prev, cudaStream_t s);
 
 // ---- row exchanges (blas3.cu) ---------------------------------------------
 // Composes the swaps ipiv[k1..k2) (1-based rows) into a list of (dst, src)
@@ -31,12 +47,25 @@ cudaError_t launch_apply_moves(T *W, long ld, const int2 *pairs, const int *npai
                                int c0, int c1, int c2, int c3, int *perm, cudaStream_t s);
 // After a factored leaf (columns [k, k+kb), rows exchanged): U = X A12 with
 // X = L11^{-1} (from the panel kernel, row-major with stride xs) on rows
-// k..k+kb of the N columns right of it, and A22 -= L21 U on the M rows
-// below, in one launch (kb <= 24 FP32 / 8 FP64, N <= 1024).  tickets: one
-// device word per 128 columns, zero before the first launch (left zero).
+// k..k+kb of the N columns starting coff after the leaf (coff a multiple of
+// 4), and A22 -= L21 U on the M rows below, in one launch (kb <= 24 FP32 /
+// 8 FP64, N <= 1024).  tickets: one device word per 128 columns, zero before
+// the first launch (left zero).
 template <typename T>
-cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int N, int M, const T *X, int xs, unsigned *tickets,
-                               cudaStream_t s);
+cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
+                               unsigned *tickets, cudaStream_t s);
+// The same leaf step BEFORE the leaf's row exchange, as a persistent launch
+// of `clusters` clusters of `cluster` CTAs (one CTA per SM): it applies the
+// leaf's row moves (pairs, *npairs) to the updated columns, to the columns
+// [0, mc1) and [mc2, mc3) and to the row permutation perm (optional).  With
+// clusters = leaf_update_rest_clusters(cluster) one cluster slot stays free
+// for a concurrent panel kernel of that cluster size.  N may be 0 (moves
+// only); M at most 786432.
+template <typename T>
+cudaError_t launch_leaf_rest(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
+                             unsigned *tickets, const int2 *pairs, const int *npairs, int mc1, int mc2, int mc3,
+                             int *perm, int clusters, int cluster, cudaStream_t s);
+template <typename T> int leaf_update_rest_clusters(int cluster);
 // Applies the moves to an int vector (the running row permutation).
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s);

@@ -23,6 +23,7 @@
 // carries the index of the row it came from; at the end the kernel writes
 // the composed row permutation as (destination, source) moves for the row
 // exchange of the rest of the matrix.
+#include <algorithm>
 #include <climits>
 #include <cstddef>
 #include <type_traits>
@@ -152,12 +153,63 @@ struct PanelSmem {
     uint64_t mbar[2];
     Cand<T> wkey[NT / 32];
     alignas(16) T wsh[NT / 32][NB];  // per-warp shifted pivot row
+    // the previous leaf applied on load (PanelPrev; its width is at most NB)
+    int redir[NT * RPT];          // local row -> row it takes its values from (INT_MIN: itself)
+    int a12src[NB];               // previous leaf's row i -> its source row (relative to row0)
+    int2 pp[2 * NB];              // its moves
+    int np;
+    T xp[NB][NB + 1];             // its X = L11^{-1}
+    T ap[NB][NB];                 // A12 rows
+    alignas(16) T up[NB][NB];     // U = X A12
 };
+
+// Columns [0, width) of rows rbase .. rbase+nvalid-1 of base (row-major, ld)
+// into fin, coalesced: consecutive threads take consecutive 16-byte pieces of
+// the rows (rows start on 16 bytes: ld and the column offsets are multiples of
+// 4 floats / 2 doubles; checked at run time all the same).  BATCH loads are
+// in flight at a time.
+template <typename T, int NB, int NT, int RPT, int BATCH>
+__device__ __forceinline__ void stage_rows(T (*fin)[NB + 1], const T *base, long ld, int rbase, int nvalid,
+                                           int width) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T), NV = NB / VW, ITEMS = RPT * NV;
+    static_assert(ITEMS % BATCH == 0, "whole batches");
+    const int tid = threadIdx.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(base) & 15) == 0;
+#pragma unroll 1
+    for (int it0 = 0; it0 < ITEMS; it0 += BATCH) {
+        V buf[BATCH];
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int idx = tid + (it0 + b) * NT, r = idx / NV, q = idx - r * NV;
+            T *pv = reinterpret_cast<T *>(&buf[b]);
+            if (r < nvalid && q * VW < width) {
+                const T *src = base + (long)(rbase + r) * ld + q * VW;
+                if (vec && (q + 1) * VW <= width) {
+                    buf[b] = *reinterpret_cast<const V *>(src);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) pv[e] = q * VW + e < width ? src[e] : T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int idx = tid + (it0 + b) * NT, r = idx / NV, q = idx - r * NV;
+            const T *pv = reinterpret_cast<const T *>(&buf[b]);
+            if (r < nvalid && q * VW < width) {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) fin[r][q * VW + e] = pv[e];
+            }
+        }
+    }
+}
 
 template <typename T, int NB, int RPT, int NT>
 __global__ void __launch_bounds__(NT, 1)
 panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32_t *__restrict__ ipiv,
-                   int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st, T *__restrict__ linv) {
+                   int2 *__restrict__ moves, int *__restrict__ nmoves, MpDevStatus *st, T *__restrict__ linv,
+                   PanelPrev<T> prev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<PanelSmem<T, NB, NT, RPT> *>(smem_raw);
     constexpr int NW = NT / 32;
@@ -185,6 +237,28 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
 
     T a[RPT][NB];
     int gi[RPT], orig[RPT];
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T), NV = NB / VW;
+    const int nvalid = max(0, min(rpc, m - rbase));  // rows of this CTA inside the panel
+    // one row into registers
+    auto load_row = [&](T (&dst)[NB], const T *row) {
+        const bool vec_ok = (reinterpret_cast<uintptr_t>(row) & 15) == 0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (vec_ok && (q + 1) * VW <= ncols) {
+                const V v = reinterpret_cast<const V *>(row)[q];
+                const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) dst[q * VW + e] = pv[e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int k = q * VW + e;
+                    dst[k] = k < ncols ? row[k] : T(0);
+                }
+            }
+        }
+    };
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
         const int r = tid + s * NT;
@@ -192,25 +266,91 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
         const bool valid = (r < rpc) && (g < m);
         gi[s] = valid ? g : INT_MAX;
         orig[s] = g;
-        const T *row = P + (long)g * ld;
-        // 16-byte loads for the whole 16-byte chunks inside ncols (rows and the
-        // panel start are 16-byte aligned: ld and the column offset are
-        // multiples of 4 floats / 2 doubles), scalar loads for the rest
-        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        constexpr int VW = 16 / sizeof(T);
-        const bool vec_ok = (reinterpret_cast<uintptr_t>(row) & 15) == 0;
+        if (valid) {
+            load_row(a[s], P + (long)g * ld);
+        } else {
 #pragma unroll
-        for (int q = 0; q < NB / VW; ++q) {
-            if (valid && vec_ok && (q + 1) * VW <= ncols) {
-                const V v = reinterpret_cast<const V *>(row)[q];
+            for (int t = 0; t < NB; ++t) a[s][t] = T(0);
+        }
+    }
+
+    // ---- 0. the previous leaf (PanelPrev): its moves, U = X A12 and
+    //         A -= L21 U.  Rows are relative to row0; its rows are -kbp .. -1.
+    //         First the moves, X and the L21 part of the local rows (staged
+    //         in fin, which the column loop fills only later), then A12 and
+    //         the rows the moves bring here.  Nothing is written to global
+    //         memory before every CTA has finished reading: U and the panel's
+    //         rows are stored after the column loop, whose first step waits
+    //         for every CTA.
+    const int kbp = prev.kb;
+    if (kbp > 0) {
+        if (tid < 2 * NB) sm.pp[tid] = prev.pairs[tid];  // slots past the count are never used
+        if (tid == 0) sm.np = min(*prev.npairs, 2 * NB);
+        for (int idx = tid; idx < kbp * kbp; idx += NT) {
+            const int i = idx / kbp, l = idx - i * kbp;
+            sm.xp[i][l] = prev.X[i * prev.xs + l];
+        }
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) sm.redir[tid + s * NT] = INT_MIN;
+        // L21: the previous leaf's columns of the local rows (in batches: the
+        // rows' values are live in registers meanwhile)
+        stage_rows<T, NB, NT, RPT, NV>(sm.fin, P - kbp, ld, rbase, nvalid, kbp);
+        if (tid < kbp) sm.a12src[tid] = tid - kbp;
+        __syncthreads();
+        for (int t = tid; t < sm.np; t += NT) {
+            const int2 mv = sm.pp[t];
+            const int d = mv.x - row0, src = mv.y - row0;
+            if (d < 0) {
+                if (d >= -kbp) sm.a12src[d + kbp] = src;
+            } else if (d >= rbase && d < rbase + rpc) {
+                sm.redir[d - rbase] = src;
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < kbp * NB; idx += NT) {
+            const int i = idx / NB, c = idx - i * NB;
+            sm.ap[i][c] = c < ncols ? P[(long)sm.a12src[i] * ld + c] : T(0);
+        }
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+            const int from = sm.redir[tid + s * NT];
+            if (gi[s] < m && from != INT_MIN) load_row(a[s], P + (long)from * ld);
+        }
+        __syncthreads();
+        // X unit lower: U row i = A12 row i + sum_{l<i} X_il A12 row l
+        for (int idx = tid; idx < kbp * NB; idx += NT) {
+            const int i = idx / NB, c = idx - i * NB;
+            T v = sm.ap[i][c];
+            for (int l = 0; l < i; ++l) v = fma(sm.xp[i][l], sm.ap[l][c], v);
+            sm.up[i][c] = v;
+        }
+        __syncthreads();
+        // A -= L21 U in the order l = 0 .. kbp-1 (each thread reads only its
+        // own staged rows of fin, before the column loop writes them); row l
+        // of U is read once for all of the thread's rows
+        for (int l = 0; l < kbp; ++l) {
+            T u[NB];
+#pragma unroll
+            for (int q = 0; q < NB / VW; ++q) {
+                const V v = reinterpret_cast<const V *>(sm.up[l])[q];
                 const T *pv = reinterpret_cast<const T *>(&v);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) a[s][q * VW + e] = pv[e];
-            } else {
+                for (int e = 0; e < VW; ++e) u[q * VW + e] = pv[e];
+            }
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const int k = q * VW + e;
-                    a[s][k] = (valid && k < ncols) ? row[k] : T(0);
+            for (int s = 0; s < RPT; ++s) {
+                const T lv = gi[s] < m ? sm.fin[tid + s * NT][l] : T(0);
+                if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                    for (int t = 0; t + 1 < NB; t += 2) {
+                        const float2 r = fma2(make_float2(-lv, -lv), make_float2(u[t], u[t + 1]),
+                                              make_float2(a[s][t], a[s][t + 1]));
+                        a[s][t] = r.x;
+                        a[s][t + 1] = r.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) a[s][t] = fma(-lv, u[t], a[s][t]);
                 }
             }
         }
@@ -393,58 +533,75 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
     if (!ok) mp_flag(st, MP_FLAG_TIMEOUT);
     __syncthreads();
     // X = L11^{-1} (unit lower, ncols x ncols; rows 0..ncols-1 are local rows
-    // of CTA 0), row-major with stride NB: thread c forms column c by
-    // substitution, x_i = -sum_{c<=l<i} l_il x_l, x_c = 1
-    if (linv && rank == 0 && tid < ncols) {
-        const int c = tid;
-        T x[NB];
+    // of CTA 0), row-major with stride NB.  Warp w forms the columns c = w,
+    // w + NW, ... by column-oriented substitution: lane i holds x_i (x = e_c),
+    // and for l = c, c+1, ... every lane i > l subtracts l_il x_l, x_l taken
+    // from lane l.
+    static_assert(NB <= 32, "one lane per row of L11");
+    if (linv && rank == 0 && warp < ncols) {
+        const int i = lane;
+        T lrow[NB];
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            T v = T(i == c ? 1 : 0);
+        for (int l = 0; l < NB; ++l) lrow[l] = (i < ncols && l < i) ? sm.fin[i][l] : T(0);
+        for (int c = warp; c < ncols; c += NW) {
+            T x = T(i == c ? 1 : 0);
 #pragma unroll
-            for (int l = 0; l < i; ++l)
-                if (l >= c) v = fma(-sm.fin[i][l], x[l], v);
-            x[i] = (i < c || i >= ncols) ? T(0) : v;
+            for (int l = 0; l < NB; ++l) {
+                const T xl = __shfl_sync(0xffffffffu, x, l);
+                if (l >= c && i > l) x = fma(-lrow[l], xl, x);
+            }
+            if (i < ncols) linv[i * NB + c] = x;
         }
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-            if (i < ncols) linv[i * NB + c] = x[i];
     }
-    // write back the finished rows and the composed permutation
+    // the previous leaf's U rows of these columns
+    if (kbp > 0 && rank == 0)
+        for (int idx = tid; idx < kbp * ncols; idx += NT) {
+            const int i = idx / ncols, c = idx - i * ncols;
+            P[(long)(i - kbp) * ld + c] = sm.up[i][c];
+        }
+    // write back the finished rows (coalesced, as stage_rows) and the
+    // composed permutation
+    {
+        const bool vec = (reinterpret_cast<uintptr_t>(P) & 15) == 0;
 #pragma unroll
-    for (int s = 0; s < RPT; ++s) {
-        if (gi[s] < m) {
-            T *row = P + (long)gi[s] * ld;
-            const T *f = sm.fin[tid + s * NT];
-            using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-            constexpr int VW = 16 / sizeof(T);
-            int k = 0;
-            if ((reinterpret_cast<uintptr_t>(row) & 15) == 0)
-                for (; k + VW <= ncols; k += VW) {
+        for (int it = 0; it < RPT * NV; ++it) {
+            const int idx = tid + it * NT, r = idx / NV, q = idx - r * NV;
+            if (r < nvalid && q * VW < ncols) {
+                T *dst = P + (long)(rbase + r) * ld + q * VW;
+                const T *src = &sm.fin[r][q * VW];
+                if (vec && (q + 1) * VW <= ncols) {
                     V v;
                     T *pv = reinterpret_cast<T *>(&v);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) pv[e] = f[k + e];
-                    *reinterpret_cast<V *>(row + k) = v;
+                    for (int e = 0; e < VW; ++e) pv[e] = src[e];
+                    *reinterpret_cast<V *>(dst) = v;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VW; ++e)
+                        if (q * VW + e < ncols) dst[e] = src[e];
                 }
-            for (; k < ncols; ++k) row[k] = f[k];
-            if (orig[s] != gi[s]) {
-                const int slot = atomicAdd(nmoves, 1);
-                moves[slot] = make_int2(row0 + gi[s], row0 + orig[s]);
             }
         }
     }
+#pragma unroll
+    for (int s = 0; s < RPT; ++s)
+        if (gi[s] < m && orig[s] != gi[s]) {
+            const int slot = atomicAdd(nmoves, 1);
+            moves[slot] = make_int2(row0 + gi[s], row0 + orig[s]);
+        }
     // no CTA may leave while a peer can still push to it
     if (CL > 1) cluster_sync_all();
 }
 
 template <typename T, int NB, int RPT>
 cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                           int *nmoves, MpDevStatus *st, T *linv, cudaStream_t s) {
+                           int *nmoves, MpDevStatus *st, T *linv, PanelPrev<T> prev, cudaStream_t s) {
     constexpr int NT = 512;
     const int cap = NT * RPT;
     const int CL = (m + cap - 1) / cap;
     if (CL < 1 || CL > 16 || ncols > NB || ncols < 1 || m < ncols) return cudaErrorInvalidValue;
+    if (prev.kb < 0 || prev.kb > NB || (prev.kb > 0 && (!prev.X || !prev.pairs || !prev.npairs)))
+        return cudaErrorInvalidValue;
     auto kern = panel_getf2_kernel<T, NB, RPT, NT>;
     const size_t smem = sizeof(PanelSmem<T, NB, NT, RPT>);
     cudaError_t e = mp_smem_attr(kern, smem);
@@ -466,7 +623,7 @@ cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     mp_note_launch();
-    return cudaLaunchKernelEx(&cfg, kern, P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv);
+    return cudaLaunchKernelEx(&cfg, kern, P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev);
 }
 
 }  // namespace
@@ -489,17 +646,27 @@ int panel_base_width<double>(int m) {
     return 4;
 }
 
+template <typename T>
+int panel_cluster_size(int m) {
+    const int rpt = m <= 16384 ? 2 : m <= 32768 ? 4 : 8;
+    return std::max(1, (m + 512 * rpt - 1) / (512 * rpt));
+}
+template int panel_cluster_size<float>(int);
+template int panel_cluster_size<double>(int);
+
 template <>
 cudaError_t launch_panel<float>(float *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                                int *nmoves, MpDevStatus *st, float *linv, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<float, 24, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
-    if (m <= 32768) return launch_panel_t<float, 16, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
-    return launch_panel_t<float, 8, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+                                int *nmoves, MpDevStatus *st, float *linv, PanelPrev<float> prev,
+                                cudaStream_t s) {
+    if (m <= 16384) return launch_panel_t<float, 24, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
+    if (m <= 32768) return launch_panel_t<float, 16, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
+    return launch_panel_t<float, 8, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
 }
 template <>
 cudaError_t launch_panel<double>(double *P, long ld, int m, int ncols, int row0, int32_t *ipiv, int2 *moves,
-                                 int *nmoves, MpDevStatus *st, double *linv, cudaStream_t s) {
-    if (m <= 16384) return launch_panel_t<double, 8, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
-    if (m <= 32768) return launch_panel_t<double, 8, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
-    return launch_panel_t<double, 4, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, s);
+                                 int *nmoves, MpDevStatus *st, double *linv, PanelPrev<double> prev,
+                                 cudaStream_t s) {
+    if (m <= 16384) return launch_panel_t<double, 8, 2>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
+    if (m <= 32768) return launch_panel_t<double, 8, 4>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
+    return launch_panel_t<double, 4, 8>(P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev, s);
 }

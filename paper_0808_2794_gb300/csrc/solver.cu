@@ -204,8 +204,8 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.W = carve(off, L.W_bytes);
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.ipiv = carve(off, sizeof(int) * (size_t)n);
-    L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, L.nb));
-    L.npairs = carve(off, sizeof(int) * 16);  // [0]: move count, [4..12): leaf tickets
+    L.pairs = carve(off, sizeof(int2) * ((size_t)2 * (size_t)std::max(n, L.nb) + 128));  // + two leaves' moves
+    L.npairs = carve(off, sizeof(int) * 32);  // [0]: move count, [4..20): leaf tickets (two sets)
     L.map = carve(off, sizeof(int) * (size_t)n);
     const size_t inv_bytes = std::max(trsv_inverse_bytes<float>(n), fp64_space ? trsv_inverse_bytes<double>(n) : 0);
     L.Linv = carve(off, inv_bytes);
@@ -221,7 +221,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
                                              : std::max(tc_workspace_bytes(n, L.nb, o.prec),
                                                         tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
-    L.linv = carve(off, 32 * 32 * sizeof(double));  // a leaf's L11^{-1}
+    L.linv = carve(off, 2 * 1024 * sizeof(double));  // two leaves' L11^{-1}
     // GMRES: Krylov basis V (m+1 columns), preconditioned vectors Z (m), small vectors
     const size_t m = o.refine == MP_REFINE_CLASSICAL ? 0 : (size_t)std::max(o.gmres_restart, 1);
     L.gV = carve(off, m ? sizeof(double) * (size_t)n * (m + 1) : 0);
@@ -298,37 +298,142 @@ cudaError_t trsm_rec(FactorCtx<T> &c, int m, int N, const T *L, long ldl, T *B, 
     return trsm_rec<T>(c, m - m1, N, L + (long)m1 * ldl + m1, ldl, B + (long)m1 * ldb, ldb);
 }
 
+// Per-device pair of internal streams for the panel: a high-priority one for
+// the chain of leaves and a low-priority one for the bulk of each leaf's
+// update (created once).
+struct PanelStreams {
+    cudaStream_t hi = nullptr, lo = nullptr;
+};
+PanelStreams panel_streams() {
+    static std::mutex mu;
+    static PanelStreams per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PanelStreams{};
+    std::lock_guard<std::mutex> g(mu);
+    PanelStreams &p = per_dev[dev];
+    if (!p.hi) {
+        int lo_pri = 0, hi_pri = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&p.hi, cudaStreamNonBlocking, hi_pri) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&p.lo, cudaStreamNonBlocking, lo_pri) != cudaSuccess)
+            p = PanelStreams{};
+    }
+    return p;
+}
+
 // LU of the outer panel, columns [k0, k0+ncols) of rows [k0, n), leaf by
-// leaf (right-looking inside the panel): a leaf of at most the base width
-// is one cluster panel kernel, followed by the exchange of its rows over all
-// other columns of W (and the running row permutation) and by one fused
-// launch that forms the leaf's rows of U for the rest of the panel and
-// updates the rows below (FP32 FMA; FP64 in the fallback).
+// leaf (right-looking inside the panel).  A leaf of at most the base width is
+// one cluster panel kernel (which also leaves L11^{-1} and its row moves);
+// the leaf's row exchange and the fused U-block + update of the panel's
+// columns right of it follow (FP32 FMA; FP64 in the fallback).
+// Leaf-level look-ahead, on two internal streams: the chain (high priority)
+// is the sequence of panel kernels, each of which first applies the previous
+// leaf's row moves and update to its own columns as it loads them.  The rest
+// of each leaf's work -- the update of the columns after the next leaf's, the
+// exchange of the columns outside the outer panel and of the row permutation
+// -- is one persistent launch on a low-priority stream, shaped in clusters so
+// that the next panel kernel always finds a free cluster slot beside it.  A
+// panel kernel waits for the bulk launch of two leaves before.  L11^{-1} and
+// the moves of two consecutive leaves live in alternating buffers.
 template <typename T>
 cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
     T *W = c.W;
     const long ld = c.ld;
     unsigned *ticket = reinterpret_cast<unsigned *>(c.npairs + 4);  // one per 128-column chunk
-    for (int k = k0; k < k0 + ncols;) {
+    PanelStreams ps_ = panel_streams();
+    cudaEvent_t ev_in = nullptr, ev_chain = nullptr, ev_rest[2] = {nullptr, nullptr};
+    bool two = ps_.hi && ps_.lo && ncols > 2 * panel_base_width<T>(c.n - k0) &&
+               leaf_update_rest_clusters<T>(panel_cluster_size<T>(c.n - k0)) > 0;
+    if (two && (cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_chain, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_rest[0], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_rest[1], cudaEventDisableTiming) != cudaSuccess)) {
+        two = false;
+    }
+    cudaStream_t user = c.s, hi = two ? ps_.hi : c.s, lo = two ? ps_.lo : c.s;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; return err == cudaSuccess; };
+    if (two) {
+        chk(cudaEventRecord(ev_in, user));
+        chk(cudaStreamWaitEvent(hi, ev_in, 0));
+        chk(cudaStreamWaitEvent(lo, ev_in, 0));
+    }
+    c.s = hi;
+    int leaf = 0, kb_prev = 0, xs_prev = 0;
+    for (int k = k0; k < k0 + ncols && err == cudaSuccess; ++leaf) {
         const int m = c.n - k;
         const int kb = std::min(panel_base_width<T>(m), k0 + ncols - k);
-        {
-            MpProfScope ps(MP_KC_PANEL, (double)m * kb * kb - (double)kb * kb * kb / 3.0, c.s);
-            CU(launch_panel<T>(W + (long)k * ld + k, ld, m, kb, k, c.ipiv + k, c.pairs, c.npairs, c.st, c.linv,
-                               c.s));
-        }
-        {
-            MpProfScope ps(MP_KC_ROWMOVES, 4.0 * kb * (double)(c.n - kb) * sizeof(T), c.s);
-            CU(launch_apply_moves<T>(W, ld, c.pairs, c.npairs, 2 * kb, 0, k, k + kb, c.n, c.perm, c.s));
-        }
+        const int xs = panel_base_width<T>(m);
         const int N = k0 + ncols - k - kb;
-        if (N > 0) {
-            MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * N + 2.0 * (m - kb) * N * kb, c.s);
-            CU(launch_leaf_update<T>(W, ld, k, kb, N, m - kb, c.linv, panel_base_width<T>(m), ticket, c.s));
+        // this leaf's L11^{-1} and row moves (alternating buffers: the
+        // previous leaf's are still read while this leaf is factored)
+        T *X = c.linv + (leaf & 1) * 1024;
+        int2 *pairs = c.pairs + (leaf & 1) * 64;
+        int *npairs = c.npairs + (leaf & 1);
+        if (!two) {
+            {
+                MpProfScope ps(MP_KC_PANEL, (double)m * kb * kb - (double)kb * kb * kb / 3.0, hi);
+                if (!chk(launch_panel<T>(W + (long)k * ld + k, ld, m, kb, k, c.ipiv + k, pairs, npairs, c.st, X,
+                                         PanelPrev<T>{}, hi)))
+                    break;
+            }
+            {
+                MpProfScope ps(MP_KC_ROWMOVES, 4.0 * kb * (double)(c.n - kb) * sizeof(T), hi);
+                if (!chk(launch_apply_moves<T>(W, ld, pairs, npairs, 2 * kb, 0, k, k + kb, c.n, c.perm, hi))) break;
+            }
+            if (N > 0) {
+                MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * N + 2.0 * (m - kb) * N * kb, hi);
+                chk(launch_leaf_update<T>(W, ld, k, kb, 0, N, m - kb, X, xs, ticket, hi));
+            }
+        } else {
+            // the bulk launch of leaf - 2 has brought these columns up to date
+            // (and released this parity's buffers); the previous leaf's moves
+            // and update are applied by the panel kernel as it loads them
+            if (leaf >= 2 && !chk(cudaStreamWaitEvent(hi, ev_rest[leaf & 1], 0))) break;
+            PanelPrev<T> pv;
+            if (leaf >= 1) {
+                pv.X = c.linv + ((leaf - 1) & 1) * 1024;
+                pv.pairs = c.pairs + ((leaf - 1) & 1) * 64;
+                pv.npairs = c.npairs + ((leaf - 1) & 1);
+                pv.xs = xs_prev;
+                pv.kb = kb_prev;
+            }
+            {
+                MpProfScope ps(MP_KC_PANEL, (double)m * kb * kb - (double)kb * kb * kb / 3.0, hi);
+                if (!chk(launch_panel<T>(W + (long)k * ld + k, ld, m, kb, k, c.ipiv + k, pairs, npairs, c.st, X, pv,
+                                         hi)))
+                    break;
+            }
+            if (!chk(cudaEventRecord(ev_chain, hi))) break;
+            if (!chk(cudaStreamWaitEvent(lo, ev_chain, 0))) break;
+            // the bulk: the columns after the next leaf's, the exchange of the
+            // columns outside the outer panel and the row permutation; in
+            // clusters of the next panel's size, leaving one such cluster free
+            const int kb_next = N > 0 ? std::min(panel_base_width<T>(m - kb), N) : 0;
+            const int cl = panel_cluster_size<T>(std::max(1, m - kb));
+            const int G = leaf_update_rest_clusters<T>(cl);
+            MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * (N - kb_next) + 2.0 * (m - kb) * (N - kb_next) * kb, lo);
+            if (!chk(launch_leaf_rest<T>(W, ld, k, kb, kb_next, N - kb_next, m - kb, X, xs, ticket + 8, pairs, npairs,
+                                         k, k0 + ncols, c.n, c.perm, std::max(1, G), cl, lo)))
+                break;
+            if (!chk(cudaEventRecord(ev_rest[leaf & 1], lo))) break;
         }
+        kb_prev = kb;
+        xs_prev = xs;
         k += kb;
     }
-    return cudaSuccess;
+    c.s = user;
+    if (two) {
+        chk(cudaEventRecord(ev_chain, hi));
+        chk(cudaStreamWaitEvent(user, ev_chain, 0));
+        chk(cudaEventRecord(ev_rest[0], lo));
+        chk(cudaStreamWaitEvent(user, ev_rest[0], 0));
+        cudaEventDestroy(ev_in);
+        cudaEventDestroy(ev_chain);
+        cudaEventDestroy(ev_rest[0]);
+        cudaEventDestroy(ev_rest[1]);
+    }
+    return err;
 }
 
 // Blocked right-looking LU: panel of width nb (recursive, rows exchanged over
@@ -339,7 +444,7 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     const int n = c.n;
     T *W = c.W;
     const long ld = c.ld;
-    CU(cudaMemsetAsync(c.npairs + 4, 0, 8 * sizeof(int), c.s));  // the leaf-update tickets
+    CU(cudaMemsetAsync(c.npairs + 4, 0, 16 * sizeof(int), c.s));  // the leaf-update tickets (two sets)
     for (int k = 0; k < n; k += nb) {
         const int nbk = std::min(nb, n - k);
         CU(getrf_panel<T>(c, k, nbk));
@@ -1159,8 +1264,8 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.status = carve(off, sizeof(StatusBlock));
     L.rowsum = carve(off, sizeof(double) * (size_t)n);
     L.perm = carve(off, sizeof(int) * (size_t)n);
-    L.pairs = carve(off, sizeof(int2) * (size_t)2 * (size_t)std::max(n, nb));
-    L.npairs = carve(off, sizeof(int) * 16);  // [0]: move count, [4..12): leaf tickets
+    L.pairs = carve(off, sizeof(int2) * ((size_t)2 * (size_t)std::max(n, nb) + 128));
+    L.npairs = carve(off, sizeof(int) * 32);  // [0]: move count, [4..20): leaf tickets (two sets)
     L.map = carve(off, sizeof(int) * (size_t)n);
     L.Linv = carve(off, trsv_inverse_bytes<float>(n));
     L.Uinv = carve(off, trsv_inverse_bytes<float>(n));
@@ -1173,7 +1278,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.tc = carve(off, prec == MP_PREC_FP32 ? 0
                                            : std::max(tc_workspace_bytes(n, nb, prec),
                                                       tc_workspace_bytes(n, nb, MP_PREC_FP16X3)));
-    L.linv = carve(off, 32 * 32 * sizeof(double));
+    L.linv = carve(off, 2 * 1024 * sizeof(double));
     L.total = align_up(off, 256);
     return L;
 }
