@@ -411,7 +411,9 @@ void or_bwd_err(int n, int nrhs, const double *A, int lda, const double *X,
 /* Convergence test (the paper leaves it open, Section 2.1; Section 3   */
 /* stops "as accurate as the full double precision" solve): x_k is      */
 /* accepted when, per column, the normwise backward error is <= tol AND */
-/* x_k has reached the FP64 floor: bwd == 0, or the last correction is  */
+/* x_k has reached the FP64 floor: bwd == 0, or bwd <= 2 u64 (then     */
+/* ||x - x_k|| <= ||A^-1|| ||r|| <= 2 kappa bwd ||x_k||, so the forward */
+/* error is at most 4 kappa u64), or the last correction is             */
 /* <= 4 u64 ||x_k||, or the corrections stopped shrinking (||z_k|| >     */
 /* stall_ratio ||z_{k-1}||, k >= 2).  The same shrink test with bwd >   */
 /* tol is a stall (Demmel et al. 2006, cited in Section 2.1).  iter     */
@@ -512,7 +514,7 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
                     int stagnant = iter >= 2 && zlast[c] > stall_ratio * znorm_prev[c];
-                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    int at_floor = bwd[c] == 0.0 || bwd[c] <= 2.0 * 0x1p-53 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
                     if (!(bwd[c] <= tol && at_floor)) done = 0;
                     if (!(bwd[c] <= tol) && stagnant) stalled = 1;
                     if (bwd[c] > worst || isnan(bwd[c])) worst = bwd[c];
@@ -580,7 +582,7 @@ int or_gesv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
                     int stagnant = iter >= 2 && zlast[c] > stall_ratio * znorm_prev[c];
-                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    int at_floor = bwd[c] == 0.0 || bwd[c] <= 2.0 * 0x1p-53 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
                     if (!(bwd[c] <= tol && at_floor)) done = 0;
                     if (bwd[c] > worst || isnan(bwd[c])) worst = bwd[c];
                 }
@@ -684,7 +686,7 @@ int or_posv_ir(int n, int nrhs, const double *A, int lda, const double *B,
                     double den = anorm * xn + bn;
                     bwd[c] = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
                     int stagnant = iter >= 2 && zlast[c] > stall_ratio * zprev[c];
-                    int at_floor = bwd[c] == 0.0 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
+                    int at_floor = bwd[c] == 0.0 || bwd[c] <= 2.0 * 0x1p-53 || zlast[c] <= 4.0 * 0x1p-53 * xn || stagnant;
                     if (!(bwd[c] <= tol && at_floor)) done = 0;
                     if (!(bwd[c] <= tol) && stagnant) stalled = 1;
                 }

@@ -516,7 +516,8 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
                     double b = den > 0.0 ? sh.rnorm[c] / den : (sh.rnorm[c] > 0.0 ? INFINITY : 0.0);
                     if (!(sh.rnorm[c] == sh.rnorm[c])) b = INFINITY;
                     const bool stagnant = it >= 2 && sh.znorm[c] > stall_ratio * sh.zprev[c];
-                    const bool at_floor = b == 0.0 || sh.znorm[c] <= 4.0 * u64 * sh.xnorm[c] || stagnant;
+                    const bool at_floor =
+                        b == 0.0 || b <= 2.0 * u64 || sh.znorm[c] <= 4.0 * u64 * sh.xnorm[c] || stagnant;
                     if (!(b <= tol)) all_tol = false;
                     if (!(b <= tol && at_floor)) done = false;
                     if (!(b <= tol) && stagnant) stalled = true;

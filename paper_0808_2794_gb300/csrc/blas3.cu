@@ -139,9 +139,9 @@ constexpr int kLeafTileCols = 128;
 // dynamic shared memory of the persistent form: a staging area (moved rows,
 // exchange tiles) and a bitmap of the moved rows of A22; more than half of an
 // SM's shared memory, so that it runs at one CTA per SM
-constexpr int kLeafStageBytes = 24 * 1024;
+constexpr int kLeafStageBytes = 40 * 1024;
 inline size_t leaf_update_pad_bytes() { return 120 * 1024; }
-constexpr int kLeafMaxBitmapRows = (120 - 24) * 1024 * 8;
+constexpr int kLeafMaxBitmapRows = (120 - 40) * 1024 * 8;
 
 template <typename T, int KBMAX, int TR>
 struct LeafSmem {
@@ -313,43 +313,168 @@ leaf_update_kernel(T *W, long ld, int k, int kb, int coff, int N, int M, const T
                                    nullptr, nullptr);
 }
 
+// ---- left-looking U rows of the previous leaf over the trailing columns ----
+// U_p = X_p (A12_p - L_p U_<p): A12_p = rows [kp, kp+kbp) of the columns
+// [tc0, tc1) (after the leaf's row exchange), L_p = the same rows of the outer
+// panel's columns [k0, kp), U_<p = rows [k0, kp) of the trailing columns (the
+// U rows of the earlier leaves), X_p = the leaf's L11^{-1}.  One item is a
+// chunk of kTrsmCols columns; the K = kp - k0 dimension streams through
+// shared memory in tiles of kTrsmK rows, two tiles in flight (cp.async).
+constexpr int kTrsmK = 32;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename T, int KBMAX>
+struct TrsmTile {
+    static constexpr int CW = 512 / sizeof(T);  // columns per item (512-byte rows)
+    __align__(16) T Lt[KBMAX][kTrsmK + 16 / sizeof(T)];
+    __align__(16) T Ut[kTrsmK][CW];
+};
+
+template <typename T, int KBMAX>
+__device__ void leaf_trsm_item(const LeafRestArgs<T> &p, int item, unsigned char *stage_raw) {
+    using Tile = TrsmTile<T, KBMAX>;
+    constexpr int CW = Tile::CW, NG = 512 / CW, RPTU = (KBMAX + NG - 1) / NG, VW = 16 / sizeof(T);
+    static_assert(2 * sizeof(Tile) <= (size_t)kLeafStageBytes, "trsm tiles exceed the staging area");
+    static_assert((size_t)KBMAX * CW * sizeof(T) <= sizeof(Tile), "T block exceeds a tile");
+    Tile *tl = reinterpret_cast<Tile *>(stage_raw);
+    const int tid = threadIdx.x, c = tid % CW, g = tid / CW;
+    const int cs = p.tc0 + item * CW, w = min(CW, p.tc1 - cs);
+    const int K = p.kp - p.k0, nkt = (K + kTrsmK - 1) / kTrsmK;
+    T *W = p.W;
+    const long ld = p.ld;
+    auto stage = [&](int t, Tile &b) {
+        const int kk0 = t * kTrsmK;
+        // L_p tile: kbp rows x kTrsmK columns of the outer panel
+        constexpr int LV = kTrsmK / VW;
+        for (int idx = tid; idx < p.kbp * LV; idx += 512) {
+            const int r = idx / LV, q = idx - r * LV;
+            const int kk = kk0 + q * VW;
+            const int valid = max(0, min(VW, K - kk));
+            // K is a multiple of VW: a piece is wholly inside or wholly outside
+            const T *src = valid > 0 ? W + (long)(p.kp + r) * ld + p.k0 + kk : W;
+            cp_async16(&b.Lt[r][q * VW], src, valid * (int)sizeof(T));
+        }
+        // U_<p tile: kTrsmK rows x CW columns
+        constexpr int UV = CW / VW;
+        for (int idx = tid; idx < kTrsmK * UV; idx += 512) {
+            const int kr = idx / UV, q = idx - kr * UV;
+            const int col = q * VW;
+            const int valid = (kk0 + kr < K) ? max(0, min(VW, w - col)) : 0;
+            const T *src = valid > 0 ? W + (long)(p.k0 + kk0 + kr) * ld + cs + col : W;
+            cp_async16(&b.Ut[kr][col], src, valid * (int)sizeof(T));  // zero-filled past valid
+        }
+    };
+    T acc[RPTU];
+#pragma unroll
+    for (int q = 0; q < RPTU; ++q) {
+        const int r = g + NG * q;
+        acc[q] = (r < p.kbp && c < w) ? W[(long)(p.kp + r) * ld + cs + c] : T(0);
+    }
+    if (nkt > 0) {
+        stage(0, tl[0]);
+        cp_async_commit();
+    }
+    for (int t = 0; t < nkt; ++t) {
+        if (t + 1 < nkt) {
+            stage(t + 1, tl[(t + 1) & 1]);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const Tile &b = tl[t & 1];
+#pragma unroll
+        for (int k4 = 0; k4 < kTrsmK; k4 += VW) {
+            T u[VW];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) u[e] = b.Ut[k4 + e][c];
+#pragma unroll
+            for (int q = 0; q < RPTU; ++q) {
+                const int r = g + NG * q;
+                if (r < p.kbp) {  // warp-uniform
+                    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+                    const V lv = *reinterpret_cast<const V *>(&b.Lt[r][k4]);
+                    const T *pl = reinterpret_cast<const T *>(&lv);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[q] = fma(-pl[e], u[e], acc[q]);
+                }
+            }
+        }
+        __syncthreads();  // the buffer is refilled two tiles on
+    }
+    // U_p = X_p T (X_p unit lower), T through shared memory
+    T(*Ts)[CW] = reinterpret_cast<T(*)[CW]>(stage_raw);
+#pragma unroll
+    for (int q = 0; q < RPTU; ++q) {
+        const int r = g + NG * q;
+        if (r < p.kbp) Ts[r][c] = acc[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPTU; ++q) {
+        const int r = g + NG * q;
+        if (r < p.kbp && c < w) {
+            T v = Ts[r][c];
+            for (int l = 0; l < r; ++l) v = fma(p.Xp[r * p.xps + l], Ts[l][c], v);
+            W[(long)(p.kp + r) * ld + cs + c] = v;
+        }
+    }
+    __syncthreads();  // Ts is reused by the next item
+}
+
 // Form (b): persistent, 128-row tiles; CTA b takes work items b, b +
-// gridDim.x, ...: first the update tiles (chunk-major, so consecutive CTAs
-// share a chunk's A12 columns in L2), then the leaf's row exchange over the
-// column ranges [0, mc1) and [mc2, mc3) (the columns outside the outer panel)
-// in chunks of kMoveBytes, then the running row permutation perm.  An
-// exchange item reads every source row of its chunk into shared memory
-// before it writes any destination row, as the moves form cycles.
+// gridDim.x, ...: first the U rows of the previous leaf over the trailing
+// columns (the longest items), then the update tiles (chunk-major, so
+// consecutive CTAs share a chunk's A12 columns in L2), then the leaf's row
+// exchange over the column ranges [0, mc1) and [mc2, mc3) (the columns
+// outside the outer panel) in chunks of kMoveBytes, then the running row
+// permutation perm.  An exchange item reads every source row of its chunk
+// into shared memory before it writes any destination row, as the moves
+// form cycles.  The previous leaf's rows are untouched by this leaf's moves
+// (they act on rows >= k only), so its U items need no ordering against them.
 constexpr int kMoveBytes = 512;
 
 template <typename T, int KBMAX>
-__global__ void __launch_bounds__(512, 1)
-leaf_update_persistent_kernel(T *W, long ld, int k, int kb, int coff, int N, int M, const T *__restrict__ X, int xs,
-                              unsigned *tickets, const int2 *__restrict__ pairs, const int *__restrict__ npairs,
-                              int mc1, int mc2, int mc3, int *perm) {
+__global__ void __launch_bounds__(512, 1) leaf_update_persistent_kernel(const LeafRestArgs<T> p) {
     __shared__ LeafSmem<T, KBMAX, 128> sm;
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     T *stage = reinterpret_cast<T *>(dyn_raw);
     unsigned *bits = reinterpret_cast<unsigned *>(dyn_raw + kLeafStageBytes);
     constexpr int CWm = kMoveBytes / sizeof(T);
+    T *W = p.W;
+    const long ld = p.ld;
+    const int k = p.k, kb = p.kb, coff = p.coff, N = p.N, M = p.M, mc1 = p.mc1, mc2 = p.mc2, mc3 = p.mc3;
+    const int2 *pairs = p.pairs;
+    int *perm = p.perm;
     const int tid = threadIdx.x;
-    const int R = max(1, (M + 127) / 128), C = N > 0 ? (N + kLeafTileCols - 1) / kLeafTileCols : 0;
+    const int NU = (p.kbp > 0 && p.tc1 > p.tc0) ? (p.tc1 - p.tc0 + TrsmTile<T, KBMAX>::CW - 1) / TrsmTile<T, KBMAX>::CW
+                                                  : 0;
+    const int R = max(1, (M + 127) / 128), C = (N > 0 && kb > 0) ? (N + kLeafTileCols - 1) / kLeafTileCols : 0;
     const int n1 = (mc1 + CWm - 1) / CWm, n2 = mc3 > mc2 ? (mc3 - mc2 + CWm - 1) / CWm : 0;
-    const int nitems = R * C + n1 + n2 + (perm ? 1 : 0);
+    const int np = p.npairs ? min(*p.npairs, 2 * KBMAX) : 0;
+    const int nitems = NU + R * C + (np > 0 ? n1 + n2 : 0) + (perm && np > 0 ? 1 : 0);
     if ((int)blockIdx.x >= nitems) return;
-    const int np = min(*npairs, 2 * KBMAX);
     // the moves: A12 sources, the moved rows of A22 (list and bitmap)
-    leaf_load_x(sm, kb, X, xs);
+    leaf_load_x(sm, kb, p.X, p.xs);
     if (tid < kb) sm.a12[tid] = k + tid;
     if (tid == 0) sm.nmv = 0;
-    const int words = (M + 31) / 32;
+    const int words = C > 0 ? (M + 31) / 32 : 0;
     for (int i = tid; i < words; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
     for (int t = tid; t < np; t += blockDim.x) {
         const int2 mv = pairs[t];
         if (mv.x < k + kb) {
             sm.a12[mv.x - k] = mv.y;
-        } else if (mv.x - (k + kb) < M) {
+        } else if (mv.x - (k + kb) < M && C > 0) {
             sm.mv[atomicAdd(&sm.nmv, 1)] = mv;
             const int rr = mv.x - (k + kb);
             atomicOr(&bits[rr >> 5], 1u << (rr & 31));
@@ -357,12 +482,17 @@ leaf_update_persistent_kernel(T *W, long ld, int k, int kb, int coff, int N, int
     }
     __syncthreads();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        if (t < R * C) {
-            const int chunk = t / R;
-            leaf_tile<T, KBMAX, 128, true>(sm, W, ld, k, kb, coff, N, M, tickets, (t - chunk * R) * 128, chunk, R,
+        if (t < NU) {
+            leaf_trsm_item<T, KBMAX>(p, t, dyn_raw);
+            continue;
+        }
+        const int t2 = t - NU;
+        if (t2 < R * C) {
+            const int chunk = t2 / R;
+            leaf_tile<T, KBMAX, 128, true>(sm, W, ld, k, kb, coff, N, M, p.tickets, (t2 - chunk * R) * 128, chunk, R,
                                            bits, stage);
-        } else if (t < R * C + n1 + n2) {
-            const int q = t - R * C;
+        } else if (t2 < R * C + n1 + n2) {
+            const int q = t2 - R * C;
             const int cs = q < n1 ? q * CWm : mc2 + (q - n1) * CWm;
             const int ce = q < n1 ? min(cs + CWm, mc1) : min(cs + CWm, mc3);
             using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -469,28 +599,26 @@ cudaError_t leaf_rest_attrs() {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_leaf_rest(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
-                             unsigned *tickets, const int2 *pairs, const int *npairs, int mc1, int mc2, int mc3,
-                             int *perm, int clusters, int cluster, cudaStream_t s) {
+cudaError_t launch_leaf_rest(const LeafRestArgs<T> &p, int clusters, int cluster, cudaStream_t s) {
     constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
     static_assert(2 * KBMAX * kMoveBytes <= kLeafStageBytes, "exchange tile exceeds the staging area");
     static_assert(2 * KBMAX * kLeafTileCols * (int)sizeof(T) <= kLeafStageBytes, "moved rows exceed the staging area");
-    if (kb <= 0 || M < 0 || N < 0 || clusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
-    if (kb > KBMAX || N > 1024 || mc1 < 0 || mc3 < mc2 || M > kLeafMaxBitmapRows) return cudaErrorInvalidValue;
+    if (p.kb < 0 || p.M < 0 || p.N < 0 || clusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
+    if (p.kb > KBMAX || p.N > 1024 || p.mc1 < 0 || p.mc3 < p.mc2 || p.M > kLeafMaxBitmapRows)
+        return cudaErrorInvalidValue;
+    if (p.kb > 0 && p.N > 0 && !p.X) return cudaErrorInvalidValue;
+    if (p.kbp < 0 || p.kbp > KBMAX || (p.kbp > 0 && (!p.Xp || p.kp < p.k0 || (p.kp - p.k0) % (16 / (int)sizeof(T)))))
+        return cudaErrorInvalidValue;
     cudaError_t e = leaf_rest_attrs<T>();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     leaf_rest_config<T>(cfg, attr, clusters, cluster, s);
     mp_note_launch();
-    return cudaLaunchKernelEx(&cfg, leaf_update_persistent_kernel<T, KBMAX>, W, ld, k, kb, coff, N, M, X, xs,
-                              tickets, pairs, npairs, mc1, mc2, mc3, perm);
+    return cudaLaunchKernelEx(&cfg, leaf_update_persistent_kernel<T, KBMAX>, p);
 }
-template cudaError_t launch_leaf_rest<float>(float *, long, int, int, int, int, int, const float *, int, unsigned *,
-                                            const int2 *, const int *, int, int, int, int *, int, int, cudaStream_t);
-template cudaError_t launch_leaf_rest<double>(double *, long, int, int, int, int, int, const double *, int,
-                                             unsigned *, const int2 *, const int *, int, int, int, int *, int, int,
-                                             cudaStream_t);
+template cudaError_t launch_leaf_rest<float>(const LeafRestArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_leaf_rest<double>(const LeafRestArgs<double> &, int, int, cudaStream_t);
 
 // Clusters of `cluster` CTAs of the persistent leaf update (one CTA per SM)
 // that fit on the device at once, minus one: the remaining slot is left for

@@ -57,14 +57,33 @@ cudaError_t launch_leaf_update(T *W, long ld, int k, int kb, int coff, int N, in
 // The same leaf step BEFORE the leaf's row exchange, as a persistent launch
 // of `clusters` clusters of `cluster` CTAs (one CTA per SM): it applies the
 // leaf's row moves (pairs, *npairs) to the updated columns, to the columns
-// [0, mc1) and [mc2, mc3) and to the row permutation perm (optional).  With
+// [0, mc1) and [mc2, mc3) and to the row permutation perm (optional).  It
+// also forms, left-looking, the U rows of the previous leaf (rows
+// [kp, kp+kbp)) over the trailing columns [tc0, tc1):
+// U_p = Xp (A12_p - L_p U_<p) with L_p = those rows of the outer panel's
+// columns [k0, kp) and U_<p = rows [k0, kp) of the trailing columns.  With
 // clusters = leaf_update_rest_clusters(cluster) one cluster slot stays free
 // for a concurrent panel kernel of that cluster size.  N may be 0 (moves
-// only); M at most 786432.
+// only), kb may be 0 (nothing but the previous leaf's U rows), npairs may be
+// null (no moves); M at most 655360.
 template <typename T>
-cudaError_t launch_leaf_rest(T *W, long ld, int k, int kb, int coff, int N, int M, const T *X, int xs,
-                             unsigned *tickets, const int2 *pairs, const int *npairs, int mc1, int mc2, int mc3,
-                             int *perm, int clusters, int cluster, cudaStream_t s);
+struct LeafRestArgs {
+    T *W = nullptr;
+    long ld = 0;
+    int k = 0, kb = 0, coff = 0, N = 0, M = 0;
+    const T *X = nullptr;
+    int xs = 0;
+    unsigned *tickets = nullptr;
+    const int2 *pairs = nullptr;
+    const int *npairs = nullptr;
+    int mc1 = 0, mc2 = 0, mc3 = 0;
+    int *perm = nullptr;
+    // the previous leaf's U rows over the trailing columns (kbp = 0: none)
+    const T *Xp = nullptr;
+    int xps = 0, kp = 0, kbp = 0, k0 = 0, tc0 = 0, tc1 = 0;
+};
+template <typename T>
+cudaError_t launch_leaf_rest(const LeafRestArgs<T> &p, int clusters, int cluster, cudaStream_t s);
 template <typename T> int leaf_update_rest_clusters(int cluster);
 // Applies the moves to an int vector (the running row permutation).
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,

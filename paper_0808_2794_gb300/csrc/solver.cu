@@ -221,7 +221,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
                                              : std::max(tc_workspace_bytes(n, L.nb, o.prec),
                                                         tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
-    L.linv = carve(off, 2 * 1024 * sizeof(double));  // two leaves' L11^{-1}
+    L.linv = carve(off, 3 * 1024 * sizeof(double));  // three leaves' L11^{-1}
     // GMRES: Krylov basis V (m+1 columns), preconditioned vectors Z (m), small vectors
     const size_t m = o.refine == MP_REFINE_CLASSICAL ? 0 : (size_t)std::max(o.gmres_restart, 1);
     L.gV = carve(off, m ? sizeof(double) * (size_t)n * (m + 1) : 0);
@@ -336,10 +336,11 @@ PanelStreams panel_streams() {
 // panel kernel waits for the bulk launch of two leaves before.  L11^{-1} and
 // the moves of two consecutive leaves live in alternating buffers.
 template <typename T>
-cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
+cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
     T *W = c.W;
     const long ld = c.ld;
     unsigned *ticket = reinterpret_cast<unsigned *>(c.npairs + 4);  // one per 128-column chunk
+    *u12_done = false;
     PanelStreams ps_ = panel_streams();
     cudaEvent_t ev_in = nullptr, ev_chain = nullptr, ev_rest[2] = {nullptr, nullptr};
     bool two = ps_.hi && ps_.lo && ncols > 2 * panel_base_width<T>(c.n - k0) &&
@@ -358,16 +359,19 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
         chk(cudaStreamWaitEvent(hi, ev_in, 0));
         chk(cudaStreamWaitEvent(lo, ev_in, 0));
     }
+    const int tc0 = k0 + ncols, tc1 = c.n;  // the trailing columns
     c.s = hi;
-    int leaf = 0, kb_prev = 0, xs_prev = 0;
+    int leaf = 0, kb_prev = 0, xs_prev = 0, k_prev = 0;
     for (int k = k0; k < k0 + ncols && err == cudaSuccess; ++leaf) {
         const int m = c.n - k;
         const int kb = std::min(panel_base_width<T>(m), k0 + ncols - k);
         const int xs = panel_base_width<T>(m);
         const int N = k0 + ncols - k - kb;
-        // this leaf's L11^{-1} and row moves (alternating buffers: the
-        // previous leaf's are still read while this leaf is factored)
-        T *X = c.linv + (leaf & 1) * 1024;
+        // this leaf's L11^{-1} (three buffers: the bulk launch of the next
+        // leaf still reads it while the leaf after that is factored) and row
+        // moves (two buffers)
+        T *X = c.linv + (leaf % 3) * 1024;
+        T *Xprev = c.linv + ((leaf + 2) % 3) * 1024;
         int2 *pairs = c.pairs + (leaf & 1) * 64;
         int *npairs = c.npairs + (leaf & 1);
         if (!two) {
@@ -392,7 +396,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
             if (leaf >= 2 && !chk(cudaStreamWaitEvent(hi, ev_rest[leaf & 1], 0))) break;
             PanelPrev<T> pv;
             if (leaf >= 1) {
-                pv.X = c.linv + ((leaf - 1) & 1) * 1024;
+                pv.X = Xprev;
                 pv.pairs = c.pairs + ((leaf - 1) & 1) * 64;
                 pv.npairs = c.npairs + ((leaf - 1) & 1);
                 pv.xs = xs_prev;
@@ -407,20 +411,65 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
             if (!chk(cudaEventRecord(ev_chain, hi))) break;
             if (!chk(cudaStreamWaitEvent(lo, ev_chain, 0))) break;
             // the bulk: the columns after the next leaf's, the exchange of the
-            // columns outside the outer panel and the row permutation; in
+            // columns outside the outer panel and of the row permutation, and
+            // the previous leaf's U rows over the trailing columns; in
             // clusters of the next panel's size, leaving one such cluster free
             const int kb_next = N > 0 ? std::min(panel_base_width<T>(m - kb), N) : 0;
             const int cl = panel_cluster_size<T>(std::max(1, m - kb));
             const int G = leaf_update_rest_clusters<T>(cl);
-            MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * (N - kb_next) + 2.0 * (m - kb) * (N - kb_next) * kb, lo);
-            if (!chk(launch_leaf_rest<T>(W, ld, k, kb, kb_next, N - kb_next, m - kb, X, xs, ticket + 8, pairs, npairs,
-                                         k, k0 + ncols, c.n, c.perm, std::max(1, G), cl, lo)))
-                break;
+            LeafRestArgs<T> ra;
+            ra.W = W;
+            ra.ld = ld;
+            ra.k = k;
+            ra.kb = kb;
+            ra.coff = kb_next;
+            ra.N = N - kb_next;
+            ra.M = m - kb;
+            ra.X = X;
+            ra.xs = xs;
+            ra.tickets = ticket + 8;
+            ra.pairs = pairs;
+            ra.npairs = npairs;
+            ra.mc1 = k;
+            ra.mc2 = tc0;
+            ra.mc3 = tc1;
+            ra.perm = c.perm;
+            if (leaf >= 1 && tc1 > tc0) {
+                ra.Xp = Xprev;
+                ra.xps = xs_prev;
+                ra.kp = k_prev;
+                ra.kbp = kb_prev;
+                ra.k0 = k0;
+                ra.tc0 = tc0;
+                ra.tc1 = tc1;
+            }
+            MpProfScope ps(MP_KC_PANELGEMM,
+                           (double)kb * kb * (N - kb_next) + 2.0 * (m - kb) * (N - kb_next) * kb +
+                               2.0 * (double)ra.kbp * (tc1 - tc0) * (k_prev - k0 + ra.kbp),
+                           lo);
+            if (!chk(launch_leaf_rest<T>(ra, std::max(1, G), cl, lo))) break;
             if (!chk(cudaEventRecord(ev_rest[leaf & 1], lo))) break;
         }
         kb_prev = kb;
         xs_prev = xs;
+        k_prev = k;
         k += kb;
+    }
+    if (two && err == cudaSuccess && tc1 > tc0) {
+        // the last leaf's U rows over the trailing columns
+        LeafRestArgs<T> ra;
+        ra.W = W;
+        ra.ld = ld;
+        ra.Xp = c.linv + ((leaf + 2) % 3) * 1024;
+        ra.xps = xs_prev;
+        ra.kp = k_prev;
+        ra.kbp = kb_prev;
+        ra.k0 = k0;
+        ra.tc0 = tc0;
+        ra.tc1 = tc1;
+        const int G = leaf_update_rest_clusters<T>(1);
+        MpProfScope ps(MP_KC_PANELGEMM, 2.0 * (double)kb_prev * (tc1 - tc0) * (k_prev - k0 + kb_prev), lo);
+        chk(launch_leaf_rest<T>(ra, std::max(1, G), 1, lo));
     }
     c.s = user;
     if (two) {
@@ -432,6 +481,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols) {
         cudaEventDestroy(ev_chain);
         cudaEventDestroy(ev_rest[0]);
         cudaEventDestroy(ev_rest[1]);
+        *u12_done = err == cudaSuccess && tc1 > tc0;
     }
     return err;
 }
@@ -447,10 +497,11 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     CU(cudaMemsetAsync(c.npairs + 4, 0, 16 * sizeof(int), c.s));  // the leaf-update tickets (two sets)
     for (int k = 0; k < n; k += nb) {
         const int nbk = std::min(nb, n - k);
-        CU(getrf_panel<T>(c, k, nbk));
+        bool u12_done = false;  // U12 formed leaf by leaf during the panel
+        CU(getrf_panel<T>(c, k, nbk, &u12_done));
         const int rest = n - k - nbk;
         if (rest > 0) {
-            {
+            if (!u12_done) {
                 MpProfScope ps(MP_KC_TRSM, (double)nbk * nbk * rest, c.s);
                 CU(trsm_rec<T>(c, nbk, rest, W + (long)k * ld + k, ld, W + (long)k * ld + k + nbk, ld));
             }
@@ -666,8 +717,9 @@ double bwd_of(const StatusBlock &h, int c) {
 
 // Refinement loop with the factors of precision T (Algorithm 1 steps 2-7).
 // x_k is accepted when every column has bwd <= tol AND has reached the FP64
-// floor (bwd == 0, last correction <= 4 u64 ||x_k||, or the corrections
-// stopped shrinking); the shrink test with bwd > tol is a stall.
+// floor (bwd == 0; bwd <= 2 u64, which bounds the forward error by
+// 2 kappa bwd <= 4 kappa u64; last correction <= 4 u64 ||x_k||; or the
+// corrections stopped shrinking); the shrink test with bwd > tol is a stall.
 // Returns 0, or a CUDA error code; *conv tells whether all columns converged.
 template <typename T>
 int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *st, bool *conv,
@@ -691,7 +743,7 @@ int refine(Solve &S, const mp_opts &o, int itermax, bool stall_test, mp_stats *s
         for (int c = 0; c < S.nrhs; ++c) {
             const double b = bwd_of(h, c);
             const bool stagnant = it >= 2 && h.znorm[c] > o.stall_ratio * zprev[c];
-            const bool at_floor = b == 0.0 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant;
+            const bool at_floor = b == 0.0 || b <= 2.0 * u64 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant;
             if (!(b <= o.tol)) all_tol = false;
             if (!(b <= o.tol && at_floor)) done = false;
             if (!(b <= o.tol) && stagnant) stalled = true;
@@ -865,7 +917,8 @@ int refine_gmres(Solve &S, const mp_opts &o, bool from_x, mp_stats *st, bool *co
             // a residual at the level at which it can be computed also marks
             // the floor: no GMRES cycle can determine a correction from it
             const bool r_floor = std::sqrt(h.rr[c]) <= 4.0 * std::sqrt((double)S.n) * u64 * h.st.anorm * h.xnorm[c];
-            const bool at_floor = b == 0.0 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant || r_floor;
+            const bool at_floor =
+                b == 0.0 || b <= 2.0 * u64 || h.znorm[c] <= 4.0 * u64 * h.xnorm[c] || stagnant || r_floor;
             cdone[c] = b <= o.tol && at_floor;
             if (!(b <= o.tol)) all_tol = false;
             if (!cdone[c]) done = false;
@@ -1278,7 +1331,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.tc = carve(off, prec == MP_PREC_FP32 ? 0
                                            : std::max(tc_workspace_bytes(n, nb, prec),
                                                       tc_workspace_bytes(n, nb, MP_PREC_FP16X3)));
-    L.linv = carve(off, 2 * 1024 * sizeof(double));
+    L.linv = carve(off, 3 * 1024 * sizeof(double));
     L.total = align_up(off, 256);
     return L;
 }
