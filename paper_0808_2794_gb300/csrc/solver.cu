@@ -167,8 +167,11 @@ enum FactorKind { kNoFactors = 0, kLuF32 = 1, kLuF64 = 2, kCholF32 = 3, kCholF64
 
 int outer_nb(int n, const mp_opts &o) {
     if (o.nb_outer > 0) return std::min(1024, std::max(32, o.nb_outer / 32 * 32));
+    // wider panels make the tensor-core trailing update more efficient, but
+    // the leaf pipeline's bulk launches (which also form U12 left-looking,
+    // K up to the panel width) then outgrow the panel kernels they overlap
     if (o.prec == MP_PREC_FP32) return n >= 4096 ? 256 : 128;
-    return n >= 8192 ? 512 : 256;
+    return n >= 8192 ? 384 : 256;
 }
 
 // ---------------------------------------------------------------------------

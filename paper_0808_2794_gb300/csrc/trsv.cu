@@ -114,9 +114,9 @@ template <> struct Vec16<double> { using type = double2; };
 // FP64, 16-byte aligned) with nrhs vectors staged in shared memory (stride BI,
 // zero beyond bs).  Each lane issues all its 16-byte loads before any FMA, so a
 // row costs one memory latency.  Returns the warp-reduced sums in every lane.
-template <typename T, bool STREAM>
+template <typename T, bool STREAM, int NR>
 __device__ __forceinline__ void row_dot(const T *__restrict__ src, int bs, const T *vs, int BI, int nrhs,
-                                        T (&sum)[kMaxRhs]) {
+                                        T (&sum)[NR]) {
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
     constexpr int STRIDE = 32 * VW;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void row_dot(const T *__restrict__ src, int bs, const
         }
     }
 #pragma unroll
-    for (int h = 0; h < kMaxRhs; ++h) {
+    for (int h = 0; h < NR; ++h) {
         T acc = T(0);
         if (h < nrhs) {
 #pragma unroll
@@ -157,8 +157,8 @@ __device__ __forceinline__ void row_dot(const T *__restrict__ src, int bs, const
     }
 }
 
-template <typename T, bool LOWER>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, bool LOWER, int NR>
+__global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
 trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ldw, const T *__restrict__ Inv,
                        const double *__restrict__ R, long ldr, const int *__restrict__ perm,
                        const double *__restrict__ rnorm, const T *__restrict__ Yin, long ldyin,
@@ -201,11 +201,11 @@ trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ld
         __syncthreads();
         const T *D = Inv + (long)b * BI * BI;
         for (int r = gwarp; r < bs; r += nwarps) {
-            T sum[kMaxRhs];
-            row_dot<T, false>(D + (long)r * BI, bs, vs, BI, nrhs, sum);
+            T sum[NR];
+            row_dot<T, false, NR>(D + (long)r * BI, bs, vs, BI, nrhs, sum);
             if (lane == 0)
 #pragma unroll
-                for (int h = 0; h < kMaxRhs; ++h)
+                for (int h = 0; h < NR; ++h)
                     if (h < nrhs) Yout[(long)h * ldyout + r0 + r] = sum[h];
         }
         if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
@@ -219,11 +219,11 @@ trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ld
         }
         __syncthreads();
         for (int r = lo + gwarp; r < hi; r += nwarps) {
-            T sum[kMaxRhs];
-            row_dot<T, true>(W + (long)r * ldw + r0, bs, vs, BI, nrhs, sum);
+            T sum[NR];
+            row_dot<T, true, NR>(W + (long)r * ldw + r0, bs, vs, BI, nrhs, sum);
             if (lane == 0)
 #pragma unroll
-                for (int h = 0; h < kMaxRhs; ++h)
+                for (int h = 0; h < NR; ++h)
                     if (h < nrhs) acc[(long)h * n + r] -= sum[h];
         }
         if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
@@ -247,15 +247,20 @@ cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, con
                               T *acc, unsigned *bar, MpDevStatus *st, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
-    auto kern = trsv_persistent_kernel<T, LOWER>;
-    const size_t smem = sizeof(T) * (size_t)kMaxRhs * BI;
+    // the right-hand-side count padded to 1, 2, 4 or 8 (fewer registers, so
+    // more rows in flight per SM)
+    auto kern = nrhs <= 1 ? trsv_persistent_kernel<T, LOWER, 1>
+                          : nrhs <= 2 ? trsv_persistent_kernel<T, LOWER, 2>
+                                      : nrhs <= 4 ? trsv_persistent_kernel<T, LOWER, 4>
+                                                  : trsv_persistent_kernel<T, LOWER, 8>;
+    const size_t smem = sizeof(T) * (size_t)(nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8) * BI;
     cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = num_sms_cached() * std::min(per_sm, 2);
+    int grid = num_sms_cached() * std::min(per_sm, 4);
     unsigned *cnt = bar, *gen = bar + 1;
     void *args[] = {(void *)&n,    (void *)&nrhs,  (void *)&BI,    (void *)&W,    (void *)&ldw,
                     (void *)&Inv,  (void *)&R,     (void *)&ldr,   (void *)&perm, (void *)&rnorm,
