@@ -42,17 +42,11 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 }
 
 // ---- thread-block cluster helpers (inline PTX, sm_90+) ---------------------
-// Two FP32 FMAs in one instruction (fma.rn.f32x2, element-wise, round to
-// nearest even): d = a * b + c lane by lane, the same bits as two fmaf calls.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
+// Two FP32 FMAs in one instruction (the paired FMA of sm_100 and later,
+// element-wise, round to nearest even): d = a * b + c lane by lane, the same
+// bits as two fmaf calls.  The builtin lets the register allocator keep the
+// operands in register pairs.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;

@@ -502,16 +502,38 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
             __syncwarp();
             using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
             constexpr int VW = 16 / sizeof(T);
+            const int act = ncols - j;  // a[.][t] with t < act are columns of the panel
 #pragma unroll
             for (int q = 0; q < NB / VW; ++q) {
+                if (q * VW >= act) continue;  // uniform: groups past the last column hold zeros
                 const V v4 = reinterpret_cast<const V *>(wsh)[q];
                 const T *pv = reinterpret_cast<const T *>(&v4);
+                if constexpr (sizeof(T) == 4) {
+                    // paired FMAs (fma.rn.f32x2, the same bits as two fmaf);
+                    // t = 0 is column j itself, already scaled
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const int t = q * VW + e;
-                    if (t >= 1) {
+                    for (int e = 0; e < VW; e += 2) {
+                        const int t = q * VW + e;
 #pragma unroll
-                        for (int s = 0; s < RPT; ++s) a[s][t] = fma(-l[s], pv[e], a[s][t]);
+                        for (int s = 0; s < RPT; ++s) {
+                            if (t == 0) {
+                                a[s][1] = fma(-l[s], pv[1], a[s][1]);
+                            } else {
+                                const float2 r = fma2(make_float2(-l[s], -l[s]), make_float2(pv[e], pv[e + 1]),
+                                                      make_float2(a[s][t], a[s][t + 1]));
+                                a[s][t] = r.x;
+                                a[s][t + 1] = r.y;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const int t = q * VW + e;
+                        if (t >= 1) {
+#pragma unroll
+                            for (int s = 0; s < RPT; ++s) a[s][t] = fma(-l[s], pv[e], a[s][t]);
+                        }
                     }
                 }
             }
