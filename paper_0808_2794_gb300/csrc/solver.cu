@@ -65,20 +65,42 @@ struct ProfRec {
 std::mutex g_prof_mu;
 unsigned g_prof_mask = 0;
 std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_prof_pool;  // recorded-and-read events, reused (creating one costs host time)
+
+cudaEvent_t prof_event() {
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        if (!g_prof_pool.empty()) {
+            cudaEvent_t e = g_prof_pool.back();
+            g_prof_pool.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+// (g_prof_mu held)
+void prof_release(const ProfRec &r) {
+    g_prof_pool.push_back(r.e0);
+    g_prof_pool.push_back(r.e1);
+}
 }  // namespace
 
 MpProfScope::MpProfScope(int cls_, double work_, cudaStream_t s_) : cls(cls_), work(work_), s(s_) {
     if (g_prof_mask & (1u << cls)) {
-        if (cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
-        else e0 = nullptr;
+        e0 = prof_event();
+        if (e0) cudaEventRecord(e0, s);
     }
 }
 MpProfScope::~MpProfScope() {
     if (!e0) return;
-    cudaEvent_t e1;
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
-    cudaEventRecord(e1, s);
+    cudaEvent_t e1 = prof_event();
     std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!e1) {
+        g_prof_pool.push_back(e0);
+        return;
+    }
+    cudaEventRecord(e1, s);
     g_prof.push_back({cls, work, e0, e1});
 }
 
@@ -107,7 +129,10 @@ cudaError_t mp_func_attr_once(const void *kern, cudaFuncAttribute attr, int valu
 
 extern "C" void mp_profile_enable(unsigned mask) {
     std::lock_guard<std::mutex> g(g_prof_mu);
-    for (auto &r : g_prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto &r : g_prof) {
+        cudaEventSynchronize(r.e1);
+        prof_release(r);
+    }
     g_prof.clear();
     g_prof_mask = mask;
 }
@@ -122,8 +147,7 @@ extern "C" int mp_profile_collect(double *ms, long long *launches, double *work)
         ms[r.cls] += t;
         launches[r.cls] += 1;
         work[r.cls] += r.work;
-        cudaEventDestroy(r.e0);
-        cudaEventDestroy(r.e1);
+        prof_release(r);
     }
     g_prof.clear();
     return 0;
