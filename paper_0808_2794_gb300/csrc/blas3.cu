@@ -175,6 +175,37 @@ __device__ __forceinline__ void leaf_tile(LeafSmem<T, KBMAX, TR> &sm, T *W, long
         const int r = idx / kb, l = idx - r * kb;
         sm.Lt[r][l] = r0 + r < M ? W[(long)(k + kb + r0 + r) * ld + k + l] : T(0);
     }
+    // this thread's 8 rows x 4 columns of the A22 tile (16-byte vectors when
+    // the 4 columns are inside the tile: the tile starts on a multiple of 4
+    // columns and ld is a multiple of 32; rows the leaf's moves replace are
+    // read but never stored).  The persistent form (one CTA per SM, nothing
+    // else to hide latency) loads them before the U computation.
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const int ty = tid >> 5, tx = tid & 31;
+    const bool full4 = tx * 4 + 3 < w;
+    const int rows = M - (r0 + ty * 8);  // rows of this thread's 8 inside A22
+    T *const tile = W + (long)(k + kb + r0 + ty * 8) * ld + (cb + tx * 4);
+    T acc[8][4];
+    auto load_tile = [&]() {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const T *src = tile + (long)a * ld;
+            if (a < rows && full4) {
+#pragma unroll
+                for (int q = 0; q < 4 / VW; ++q) {
+                    const V v = reinterpret_cast<const V *>(src)[q];
+                    const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = (a < rows && tx * 4 + b < w) ? src[b] : T(0);
+            }
+        }
+    };
+    if constexpr (MOVES) load_tile();
     __syncthreads();
     // U = X A12 for the chunk's columns: thread (g, c) forms rows g, g+NG, ...
     // of column c (independent dot products, l in order)
@@ -196,33 +227,8 @@ __device__ __forceinline__ void leaf_tile(LeafSmem<T, KBMAX, TR> &sm, T *W, long
         }
     }
     __syncthreads();
-    // this thread's 8 rows x 4 columns of the A22 tile (16-byte vectors when
-    // the 4 columns are inside the tile: the tile starts on a multiple of 4
-    // columns and ld is a multiple of 32)
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    constexpr int VW = 16 / sizeof(T);
     {
-        const int ty = tid >> 5, tx = tid & 31;
-        const bool full4 = tx * 4 + 3 < w;
-        const int rows = M - (r0 + ty * 8);  // rows of this thread's 8 inside A22
-        T *const tile = W + (long)(k + kb + r0 + ty * 8) * ld + (cb + tx * 4);
-        T acc[8][4];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const T *src = tile + (long)a * ld;
-            if (a < rows && full4) {
-#pragma unroll
-                for (int q = 0; q < 4 / VW; ++q) {
-                    const V v = reinterpret_cast<const V *>(src)[q];
-                    const T *pv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) acc[a][q * VW + e] = pv[e];
-                }
-            } else {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = (a < rows && tx * 4 + b < w) ? src[b] : T(0);
-            }
-        }
+        if constexpr (!MOVES) load_tile();
         for (int l = 0; l < kb; ++l) {
             T bv[4], av[8];
 #pragma unroll

@@ -118,15 +118,33 @@ def test_getrf_fp32_pivots_exact(torch, mp, orc, n):
     assert np.max(np.abs(LU - LUo.astype(np.float64))) <= 64 * n * U32 * scale
 
 
-@pytest.mark.parametrize("n,nb", [(100, 32), (700, 128), (1024, 0), (2000, 256)])
+@pytest.mark.parametrize("n,nb", [(100, 32), (700, 128), (1024, 0), (2000, 256), (1500, 384), (2500, 448)])
 def test_getrf_fp32_random_invariants(torch, mp, orc, n, nb):
     A, _, _ = inputs.dense_system(n, seed=n + 1)
     _, LU, piv, info, flags = _factor(torch, mp, A, nb_outer=nb)
     assert info == 0 and flags == 0
     _check_factors(A, LU, piv, U32, c=16.0)
-    # pivots agree with the oracle wherever the oracle's choice is not a near tie
+    # pivots agree with the oracle up to the first column where the two
+    # choices are a near tie: there the candidates' magnitudes in the FP64
+    # Schur complement (under the oracle's earlier pivots) agree to rounding
     _, pivo, _ = orc.getrf(A, prec=32)
-    assert np.mean(piv == pivo) > 0.95
+    _assert_pivots_until_near_tie(A, np.asarray(piv), np.asarray(pivo), tol=64 * n * U32)
+
+
+def _assert_pivots_until_near_tie(A, piv, pivo, tol):
+    diff = np.nonzero(piv != pivo)[0]
+    if diff.size == 0:
+        return
+    j = int(diff[0])
+    n = A.shape[0]
+    perm = np.arange(n)
+    for k in range(j):  # the oracle's row interchanges for columns 0 .. j-1
+        q = pivo[k] - 1
+        perm[[k, q]] = perm[[q, k]]
+    PA = A[perm]
+    s = PA[j:, j] - PA[j:, :j] @ np.linalg.solve(PA[:j, :j], PA[:j, j]) if j > 0 else PA[j:, j]
+    a_gpu, a_orc = abs(s[piv[j] - 1 - j]), abs(s[pivo[j] - 1 - j])
+    assert abs(a_gpu - a_orc) <= tol * max(a_gpu, a_orc), (j, a_gpu, a_orc)
 
 
 def test_getrf_zero_pivot_reports_info(torch, mp):
@@ -250,6 +268,22 @@ def test_gesv_itermax_zero_forces_fallback(torch, mp, orc):
     assert np.all(orc.bwd_err(A, host(X), B) <= 1e-14)
     X, piv, st = mp.gesv(dev(torch, A), dev(torch, B), itermax=0, allow_fallback=False)
     assert st["flags"] & mp.FLAG_NOT_CONVERGED
+
+
+def test_gesv_fp64_fallback_factorization(torch, mp, orc):
+    """itermax = 0 forces the FP64 fallback: the FP64 LU runs through the same
+    leaf pipeline as the low-precision one (panel kernel applying the previous
+    leaf on load, bulk launches with the left-looking U rows), here over
+    several 128-wide outer panels with a ragged last one.  The FP64 solve is
+    compared with the oracle's FP64 solve."""
+    n = 1000
+    A, B, _ = inputs.dense_system(n, nrhs=2, seed=12)
+    X, piv, st = mp.gesv(dev(torch, A), dev(torch, B), itermax=0, nb_outer=128)
+    assert st["flags"] & mp.FLAG_FALLBACK
+    X = host(X).reshape(n, 2)
+    assert np.all(orc.bwd_err(A, X, B) <= 1e-14)
+    ref = orc.gesv_ir(A, B, factor_prec=64)["X"].reshape(n, 2)
+    assert np.max(np.abs(X - ref)) / np.max(np.abs(ref)) <= 10 * orc.kappa_inf(A) * U64
 
 
 def test_gesv_singular_reports_info(torch, mp):
