@@ -43,6 +43,27 @@ def test_dense_lu_n16384_bench_configuration(torch, mp, orc):
     assert np.max(np.abs(X[:, 0] - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-9
 
 
+@pytest.mark.parametrize("n", [20480, 33024])
+def test_dense_lu_tall_panel_variants(torch, mp, n):
+    """Sizes whose first leaves are taller than 16384 rows (16-column leaves,
+    4 rows per thread) and, at n = 33024, taller than 32768 rows (8-column
+    leaves, 8 rows per thread), so the panel kernel's taller variants run the
+    whole leaf pipeline.  Too large for the CPU oracle: the backward error
+    comes from the library's FP64 residual (checked against the oracle at the
+    other sizes), the forward error from the known x_true."""
+    A, B, X_true = inputs.dense_system(n, seed=3)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    del A
+    X, piv, st = mp.gesv(Ad, Bd)
+    assert st["flags"] == 0, st
+    R = mp.residual(Ad, X.reshape(n, 1), Bd.reshape(n, 1))
+    anorm = float(torch.linalg.matrix_norm(Ad, ord=float("inf")))
+    bwd = float(R.abs().max()) / (anorm * float(X.abs().max()) + float(Bd.abs().max()))
+    assert bwd <= 1e-14, (bwd, st)
+    X = X.cpu().numpy().reshape(n)
+    assert np.max(np.abs(X - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-8
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e8])
 def test_spd_n4096_fp16_prescribed_kappa(torch, mp, orc, kappa):
     """SPD systems of prescribed condition number (the paper's Fig. 4
