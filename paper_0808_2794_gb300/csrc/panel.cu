@@ -8,21 +8,31 @@
 // position after every column, so that the current column is always a[0] and
 // the loop over columns is a rolled loop with static register indices (the
 // body stays in the instruction cache).  Finished values (the L part and the
-// U rows) go to shared memory.  Per column:
-//   1. each thread finds its local candidate, warps reduce with shuffles
+// U rows) go to shared memory.
+//
+// Prologue (optional, PanelPrev): the previous leaf of the same outer panel
+// is applied to the panel's columns as they are loaded.  Rows are taken
+// through that leaf's moves, U = X A12 is formed (X = its L11^{-1}), and
+// A -= L21 U, so the panel is the only kernel on the critical path of a leaf.
+//
+// Per column:
+//   1. each thread finds its local candidate and warps reduce with shuffles
 //      (largest magnitude, ties to the smallest row index, NaN counted as
-//      infinite so it is chosen and reported as a breakdown); the winning
-//      lane publishes its whole row in a per-warp slot, the owner of the
-//      diagonal row publishes that row;                    -- CTA barrier
-//   2. warp 0 reduces the warp candidates;                 -- cluster barrier
-//   3. every warp reads the CTA candidates of the cluster and the winning and
-//      diagonal rows through distributed shared memory, then rows are
-//      exchanged, the column is scaled (true division) and the rank-1 update
-//      is applied to the active columns.
-// Slots are double-buffered, so two barriers per column suffice.  Every row
-// carries the index of the row it came from; at the end the kernel writes
-// the composed row permutation as (destination, source) moves for the row
-// exchange of the rest of the matrix.
+//      infinite so it is chosen and reported as a breakdown); the warp
+//      candidates meet in shared memory                    -- CTA barrier
+//   2. the warp holding the CTA's candidate row and the warp holding the
+//      diagonal row push those rows into every CTA of the cluster
+//      (st.async into distributed shared memory, counted on the receiver's
+//      mbarrier; slots double-buffered by column)
+//   3. every CTA waits on its mbarrier (bounded: a timeout sets a status flag
+//      instead of hanging), picks the cluster's pivot, exchanges rows, scales
+//      the column (true division) and applies the rank-1 update to the
+//      active columns (paired FMAs; groups past the panel's edge skipped).
+// Epilogue: X = L11^{-1} (warp-per-column substitution with shuffles), the
+// previous leaf's U rows, the finished rows written back coalesced, and the
+// composed row permutation as (destination, source) moves for the row
+// exchange of the rest of the matrix.  Every row carries the index of the row
+// it came from.
 #include <algorithm>
 #include <climits>
 #include <cstddef>
