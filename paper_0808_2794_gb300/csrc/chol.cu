@@ -17,11 +17,12 @@
 namespace {
 
 constexpr int kLeaf = 32;      // leaf width (columns)
-constexpr int kLeafRows = 256; // rows below the diagonal block per CTA (one per thread)
+constexpr int kLeafRows = 128; // rows below the diagonal block per CTA (one per thread)
 
-// Rows [k0, n) x columns [k0, k0 + nc) of W, nc <= kLeaf.  Every CTA
-// factors the diagonal block in shared memory (the same arithmetic in each,
-// so the copies agree bit for bit); CTA 0 writes it back.  Then each thread
+// Rows [k0, n) x columns [k0, k0 + nc) of W, nc <= kLeaf.  In every CTA,
+// warp 0 factors the diagonal block in registers, one row per lane, taking
+// the column entries of other rows by shuffle (the same arithmetic in each
+// CTA, so the copies agree bit for bit); CTA 0 writes it back.  Then each thread
 // takes one row below the block and solves x L11^T = a by forward
 // substitution.  A non-positive or non-finite pivot sets LOWP_BREAKDOWN and
 // the first such column (1-based) in zero_pivot; the pivot is replaced by 1
@@ -45,41 +46,60 @@ potrf_leaf_kernel(int n, int k0, int nc, T *__restrict__ W, long ldw, MpDevStatu
         Rs[r][j] = W[(long)(rbase + r) * ldw + k0 + j];
     }
     __syncthreads();
-    // POTF2 on the diagonal block, right-looking
-    for (int j = 0; j < nc; ++j) {
-        T d = Ls[j][j];
-        if (!(d > T(0)) || !(d < T(INFINITY))) {
-            if (blockIdx.x == 0 && tid == 0) {
-                mp_flag(st, MP_FLAG_LOWP_BREAKDOWN);
-                atomicCAS(&st->zero_pivot, 0, k0 + j + 1);
+    // POTF2 on the diagonal block, right-looking, by warp 0: lane i holds row i
+    static_assert(kLeaf == 32, "one lane per row of the diagonal block");
+    if (tid < 32) {
+        const int i = tid;
+        T b[kLeaf];
+#pragma unroll
+        for (int c = 0; c < kLeaf; ++c) b[c] = Ls[i][c];
+#pragma unroll
+        for (int j = 0; j < kLeaf; ++j) {
+            if (j >= nc) break;  // uniform
+            T d = __shfl_sync(0xffffffffu, b[j], j);
+            if (!(d > T(0)) || !(d < T(INFINITY))) {
+                if (blockIdx.x == 0 && i == 0) {
+                    mp_flag(st, MP_FLAG_LOWP_BREAKDOWN);
+                    atomicCAS(&st->zero_pivot, 0, k0 + j + 1);
+                }
+                d = T(1);
             }
-            d = T(1);
+            const T ljj = sqrt(d);
+            if (i == j) b[j] = ljj;
+            else if (i > j && i < nc) b[j] = b[j] / ljj;
+            // a_ic -= l_ij l_cj for j < c <= i < nc
+#pragma unroll
+            for (int c = j + 1; c < kLeaf; ++c) {
+                const T lcj = __shfl_sync(0xffffffffu, b[j], c);
+                if (c <= i && i < nc) b[c] = fma(-b[j], lcj, b[c]);
+            }
         }
-        const T ljj = sqrt(d);
-        __syncthreads();
-        if (tid == 0) Ls[j][j] = ljj;
-        if (tid > j && tid < nc) Ls[tid][j] = Ls[tid][j] / ljj;
-        __syncthreads();
-        // a_ic -= l_ij l_cj for j < c <= i < nc
-        const int m = nc - j - 1;
-        for (int idx = tid; idx < m * m; idx += blockDim.x) {
-            const int i = j + 1 + idx / m, c = j + 1 + idx % m;
-            if (c <= i) Ls[i][c] = fma(-Ls[i][j], Ls[c][j], Ls[i][c]);
-        }
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kLeaf; ++c) Ls[i][c] = b[c];
     }
+    __syncthreads();
     if (blockIdx.x == 0)
         for (int idx = tid; idx < nc * nc; idx += blockDim.x) {
             const int i = idx / nc, j = idx % nc;
             if (j <= i) W[(long)(k0 + i) * ldw + k0 + j] = Ls[i][j];
         }
-    // rows below: x_j = (a_j - sum_{p<j} x_p l_jp) / l_jj
+    // rows below: x_j = (a_j - sum_{p<j} x_p l_jp) / l_jj, the row in
+    // registers (the loads of L are independent of the chain)
     if (tid < nrows) {
-        for (int j = 0; j < nc; ++j) {
-            T s = Rs[tid][j];
-            for (int p = 0; p < j; ++p) s = fma(-Rs[tid][p], Ls[j][p], s);
-            Rs[tid][j] = s / Ls[j][j];
+        T x[kLeaf];
+#pragma unroll
+        for (int j = 0; j < kLeaf; ++j) x[j] = j < nc ? Rs[tid][j] : T(0);
+#pragma unroll
+        for (int j = 0; j < kLeaf; ++j) {
+            if (j >= nc) break;  // uniform
+            T s = x[j];
+#pragma unroll
+            for (int p = 0; p < j; ++p) s = fma(-x[p], Ls[j][p], s);
+            x[j] = s / Ls[j][j];
         }
+#pragma unroll
+        for (int j = 0; j < kLeaf; ++j)
+            if (j < nc) Rs[tid][j] = x[j];
     }
     __syncthreads();
     for (int idx = tid; idx < nrows * nc; idx += blockDim.x) {
