@@ -57,6 +57,47 @@ def load_peaks():
     return d
 
 
+# Nominal FP64 rate of GB300 (dense, CUDA cores): the residual's one FP64 FMA
+# per 8-byte element of A runs against it rather than against HBM.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def class_rooflines(prof, peaks, prec, n, nrhs):
+    """Roofline of every timed kernel class of one solve: prof maps class ->
+    (ms, launches, work) as the library's profiler reports it (work in flops
+    for the factorization classes, in bytes for the triangular solves, the
+    residual and the row exchanges).  Each class gets the bound that applies
+    to it on GB300: the tensor pipe for the low-precision trailing update,
+    FP32 CUDA cores for the panel and the FP32 updates, HBM for the
+    triangular solves and row exchanges, and the FP64 pipe for the residual
+    (2 n^2 nrhs FP64 flops per launch, one FMA per element of A and column)."""
+    smx = peaks.get("sm_max_mhz", 2070.0)
+    fp32 = 152 * 128 * 2 * smx * 1e6 / 1e12
+    out = {}
+    for cls, (ms, nl, work) in prof.items():
+        if ms <= 0 or nl <= 0:
+            continue
+        if cls == "update" and prec in ("bf16", "fp16", "fp16x3", "e4m3"):
+            bound, unit, peak, src = "tensor", "TFLOP/s", peaks.get("bf16_tflops_sustained", 1700.0), peaks["_source"]
+            if prec == "fp16x3":
+                work = 3.0 * work  # three products per k-step on the tensor pipe
+            elif prec == "e4m3":
+                peak = 2.0 * peak  # fp8 runs at twice the bf16 rate
+            achieved = work / (ms * 1e-3) / 1e12
+        elif cls in ("panel", "panelgemm", "trsm", "update"):
+            bound, unit, peak, src = "alu", "TFLOP/s", fp32, "sm_max_mhz x 152 SM x 128 lanes x 2"
+            achieved = work / (ms * 1e-3) / 1e12
+        elif cls == "residual":
+            bound, unit, peak, src = "alu", "TFLOP/s", FP64_NOMINAL_TFLOPS, "nominal FP64"
+            achieved = nl * 2.0 * n * n * nrhs / (ms * 1e-3) / 1e12
+        else:
+            bound, unit, peak, src = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0), peaks["_source"]
+            achieved = work / (ms * 1e-3) / 1e9
+        out[cls] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak if peak else None, "ms": ms, "launches": nl, "peak_source": src}
+    return out
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -373,6 +414,7 @@ def main():
                 "kernel": dom, "share_of_step": share, "launches_timed": nl_d,
                 "peak_source": peaks["_source"]}
     breakdown = {c: round(v[0] / max(1, 1), 3) for c, v in prof0.items()}
+    by_class = class_rooflines(prof0, peaks, args.prec, n, nrhs)
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -431,6 +473,7 @@ def main():
                       "ms_convert": last["ms_convert"], "ms_factor": last["ms_factor"],
                       "ms_refine": last["ms_refine"], "ms_fallback": last["ms_fallback"]},
             "kernel_ms_first_warmup": breakdown,
+            "rooflines_by_class": by_class,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
