@@ -19,7 +19,11 @@
  *   - A and B are read-only.  X is output-only and must not overlap A or B.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is stream-ordered; a call returns after reading back the
- *     small status block (iterations, flags), so X is valid on return.
+ *     small status block (iterations, flags), so X is valid on return.  The
+ *     LU factorization forks its leaf pipeline onto two internal streams of
+ *     the library (one of high, one of low priority, created on a device's
+ *     first factorization) and joins them back into `stream` by events, so
+ *     the ordering with respect to `stream` is unchanged.
  *   - Pivots are LAPACK style: int32, 1-based, row i was exchanged with row
  *     ipiv[i], applied for i = 0..n-1 in order.
  *   - Return value: 0 success; -i if argument i (1-based) is illegal
@@ -203,8 +207,9 @@ MP_API int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const dou
  * (device pointers, as for mp_gesv); the call allocates nothing.
  *   - Sizes whose mp_gesv_workspace_bytes(n, nrhs, opts) exceed the array
  *     return -1 with an explanatory mp_last_error().
- *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *   - The first call on a device looks up the array's device address and
+ *     creates the internal streams (with that device current); make that
+ *     first call before any stream capture.
  *   - Every call on a device shares the one array and it keeps the previous
  *     call's contents; the solver re-initializes everything it needs.  Calls
  *     that overlap on the GPU (different streams or host threads) race on the
