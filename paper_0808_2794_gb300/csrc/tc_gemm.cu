@@ -505,11 +505,16 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     cudaError_t e;
     if (SCALED) {
         if (SPLIT == 2) {
-            // padding rows of the hi halves must be zero
-            e = cudaMemsetAsync(Ap, 0, (size_t)2 * a_lo * Kpad * sizeof(H), s);
-            if (e != cudaSuccess) return e;
-            e = cudaMemsetAsync(Bp, 0, (size_t)2 * b_lo * Kpad * sizeof(H), s);
-            if (e != cudaSuccess) return e;
+            // the padding rows of both halves (up to the tile multiple) must be
+            // zero; the pack kernels write every other element, K padding included
+            auto zero_rows = [&](H *base, long r0, long r1) {
+                return r1 > r0 ? cudaMemsetAsync(base + r0 * Kpad, 0, (size_t)(r1 - r0) * Kpad * sizeof(H), s)
+                               : cudaSuccess;
+            };
+            if ((e = zero_rows(Ap, N, a_lo)) != cudaSuccess) return e;
+            if ((e = zero_rows(Ap, a_lo + N, 2 * a_lo)) != cudaSuccess) return e;
+            if ((e = zero_rows(Bp, M, b_lo)) != cudaSuccess) return e;
+            if ((e = zero_rows(Bp, b_lo + M, 2 * b_lo)) != cudaSuccess) return e;
         }
         e = cudaMemsetAsync(w.umax, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
