@@ -349,6 +349,7 @@ __device__ void leaf_trsm_item(const LeafRestArgs<T> &p, int item, unsigned char
     using Tile = TrsmTile<T, KBMAX>;
     constexpr int CW = Tile::CW, NG = 512 / CW, RPTU = (KBMAX + NG - 1) / NG, VW = 16 / sizeof(T);
     static_assert(2 * sizeof(Tile) <= (size_t)kLeafStageBytes, "trsm tiles exceed the staging area");
+    static_assert(sizeof(T) * KBMAX * CW + 4 * (512 / 32) <= 2 * sizeof(Tile), "U block and warp maxima exceed two tiles");
     static_assert((size_t)KBMAX * CW * sizeof(T) <= sizeof(Tile), "T block exceeds a tile");
     Tile *tl = reinterpret_cast<Tile *>(stage_raw);
     const int tid = threadIdx.x, c = tid % CW, g = tid / CW;
@@ -425,6 +426,7 @@ __device__ void leaf_trsm_item(const LeafRestArgs<T> &p, int item, unsigned char
         if (r < p.kbp) Ts[r][c] = acc[q];
     }
     __syncthreads();
+    float vmax = 0.f;  // max |U| of this thread's values (NaN counted as infinite)
 #pragma unroll
     for (int q = 0; q < RPTU; ++q) {
         const int r = g + NG * q;
@@ -432,6 +434,20 @@ __device__ void leaf_trsm_item(const LeafRestArgs<T> &p, int item, unsigned char
             T v = Ts[r][c];
             for (int l = 0; l < r; ++l) v = fma(p.Xp[r * p.xps + l], Ts[l][c], v);
             W[(long)(p.kp + r) * ld + cs + c] = v;
+            const float a = fabsf((float)v);
+            vmax = (a > vmax || a != a) ? ((a != a) ? INFINITY : a) : vmax;
+        }
+    }
+    if (p.umax) {  // one atomic per item: warps, then the CTA
+        float *wm = reinterpret_cast<float *>(stage_raw + sizeof(T) * KBMAX * CW);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+        if ((tid & 31) == 0) wm[tid >> 5] = vmax;
+        __syncthreads();
+        if (tid == 0) {
+            float m = 0.f;
+            for (int i = 0; i < 512 / 32; ++i) m = fmaxf(m, wm[i]);
+            atomicMax(p.umax, __float_as_uint(m));
         }
     }
     __syncthreads();  // Ts is reused by the next item

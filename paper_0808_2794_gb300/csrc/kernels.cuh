@@ -81,6 +81,9 @@ struct LeafRestArgs {
     // the previous leaf's U rows over the trailing columns (kbp = 0: none)
     const T *Xp = nullptr;
     int xps = 0, kp = 0, kbp = 0, k0 = 0, tc0 = 0, tc1 = 0;
+    // optional: running max |U| of those rows (uint bits of a non-negative
+    // float, NaN counted as infinite), atomically raised
+    unsigned *umax = nullptr;
 };
 template <typename T>
 cudaError_t launch_leaf_rest(const LeafRestArgs<T> &p, int clusters, int cluster, cudaStream_t s);

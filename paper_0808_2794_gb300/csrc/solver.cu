@@ -232,7 +232,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.ipiv = carve(off, sizeof(int) * (size_t)n);
     L.pairs = carve(off, sizeof(int2) * ((size_t)2 * (size_t)std::max(n, L.nb) + 128));  // + two leaves' moves
-    L.npairs = carve(off, sizeof(int) * 32);  // [0]: move count, [4..20): leaf tickets (two sets)
+    L.npairs = carve(off, sizeof(int) * 32);  // [0], [1]: two leaves' move counts, [2]: max |U12|, [4..20): tickets
     L.map = carve(off, sizeof(int) * (size_t)n);
     const size_t inv_bytes = std::max(trsv_inverse_bytes<float>(n), fp64_space ? trsv_inverse_bytes<double>(n) : 0);
     L.Linv = carve(off, inv_bytes);
@@ -363,11 +363,12 @@ PanelStreams panel_streams() {
 // panel kernel waits for the bulk launch of two leaves before.  L11^{-1} and
 // the moves of two consecutive leaves live in alternating buffers.
 template <typename T>
-cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
+cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsigned **u12_max) {
     T *W = c.W;
     const long ld = c.ld;
     unsigned *ticket = reinterpret_cast<unsigned *>(c.npairs + 4);  // one per 128-column chunk
     *u12_done = false;
+    if (u12_max) *u12_max = nullptr;
     PanelStreams ps_ = panel_streams();
     cudaEvent_t ev_in = nullptr, ev_chain = nullptr, ev_rest[2] = {nullptr, nullptr};
     bool two = ps_.hi && ps_.lo && ncols > 2 * panel_base_width<T>(c.n - k0) &&
@@ -387,6 +388,12 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
         chk(cudaStreamWaitEvent(lo, ev_in, 0));
     }
     const int tc0 = k0 + ncols, tc1 = c.n;  // the trailing columns
+    // max |U12| for the scaled tensor-core rungs, raised as U12 is formed
+    unsigned *umax = (two && sizeof(T) == 4 && c.prec != MP_PREC_FP32 && tc1 > tc0)
+                         ? reinterpret_cast<unsigned *>(c.npairs + 2)
+                         : nullptr;
+    // zeroed on the bulk stream, ahead of every launch that raises it
+    if (umax && err == cudaSuccess) chk(cudaMemsetAsync(umax, 0, sizeof(unsigned), lo));
     c.s = hi;
     int leaf = 0, kb_prev = 0, xs_prev = 0, k_prev = 0;
     for (int k = k0; k < k0 + ncols && err == cudaSuccess; ++leaf) {
@@ -469,6 +476,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
                 ra.k0 = k0;
                 ra.tc0 = tc0;
                 ra.tc1 = tc1;
+                ra.umax = umax;
             }
             MpProfScope ps(MP_KC_PANELGEMM,
                            (double)kb * kb * (N - kb_next) + 2.0 * (m - kb) * (N - kb_next) * kb +
@@ -494,6 +502,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
         ra.k0 = k0;
         ra.tc0 = tc0;
         ra.tc1 = tc1;
+        ra.umax = umax;
         const int G = leaf_update_rest_clusters<T>(1);
         MpProfScope ps(MP_KC_PANELGEMM, 2.0 * (double)kb_prev * (tc1 - tc0) * (k_prev - k0 + kb_prev), lo);
         chk(launch_leaf_rest<T>(ra, std::max(1, G), 1, lo));
@@ -509,6 +518,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done) {
         cudaEventDestroy(ev_rest[0]);
         cudaEventDestroy(ev_rest[1]);
         *u12_done = err == cudaSuccess && tc1 > tc0;
+        if (u12_max) *u12_max = *u12_done ? umax : nullptr;
     }
     return err;
 }
@@ -525,7 +535,8 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
     for (int k = 0; k < n; k += nb) {
         const int nbk = std::min(nb, n - k);
         bool u12_done = false;  // U12 formed leaf by leaf during the panel
-        CU(getrf_panel<T>(c, k, nbk, &u12_done));
+        unsigned *u12_max = nullptr;  // and its max |.|, when taken on the way
+        CU(getrf_panel<T>(c, k, nbk, &u12_done, &u12_max));
         const int rest = n - k - nbk;
         if (rest > 0) {
             if (!u12_done) {
@@ -539,7 +550,7 @@ cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
             if (sizeof(T) == 4 && c.prec != MP_PREC_FP32) {
                 CU(tc_trailing_update(c.prec, rest, rest, nbk, reinterpret_cast<const float *>(L21), ld,
                                       reinterpret_cast<const float *>(U12), ld,
-                                      reinterpret_cast<float *>(A22), ld, c.tc, c.st, c.s));
+                                      reinterpret_cast<float *>(A22), ld, c.tc, c.st, c.s, u12_max));
             } else {
                 CU(launch_gemm_sub<T>(rest, rest, nbk, L21, ld, U12, ld, A22, ld, c.s));
             }
@@ -1345,7 +1356,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.rowsum = carve(off, sizeof(double) * (size_t)n);
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.pairs = carve(off, sizeof(int2) * ((size_t)2 * (size_t)std::max(n, nb) + 128));
-    L.npairs = carve(off, sizeof(int) * 32);  // [0]: move count, [4..20): leaf tickets (two sets)
+    L.npairs = carve(off, sizeof(int) * 32);  // [0], [1]: two leaves' move counts, [2]: max |U12|, [4..20): tickets
     L.map = carve(off, sizeof(int) * (size_t)n);
     L.Linv = carve(off, trsv_inverse_bytes<float>(n));
     L.Uinv = carve(off, trsv_inverse_bytes<float>(n));

@@ -401,18 +401,19 @@ absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigne
 }
 
 // Power-of-two scales: sU = 2^(top - ceil(log2 max|U|)) and sL = 2^(top - 1)
-// when |l| <= 1 (partial pivoting), else sL from max|L| (umax_bits[1]) like
+// when |l| <= 1 (partial pivoting), else sL from max|L| (lmax_bits) like
 // sU; top = 14 for the split fp16 operands (below 65504), 8 for E4M3 (below
 // 448); writes sL, sU and 1 / (sL sU).
-__global__ void split_scales_kernel(const unsigned *umax_bits, float *scales, int l_from_max, int top) {
+__global__ void split_scales_kernel(const unsigned *umax_bits, const unsigned *lmax_bits, float *scales,
+                                    int l_from_max, int top) {
     auto scale_exp = [top](unsigned bits) {
         const float m = __uint_as_float(bits);
         int e = 0;
         if (m > 0.f && m < INFINITY) frexpf(m, &e);  // m < 2^e
         return top - e;
     };
-    const int eu = scale_exp(umax_bits[0]);
-    const int el = l_from_max ? scale_exp(umax_bits[1]) : top - 1;
+    const int eu = scale_exp(*umax_bits);
+    const int el = l_from_max ? scale_exp(*lmax_bits) : top - 1;
     scales[0] = ldexpf(1.0f, el);
     scales[1] = ldexpf(1.0f, eu);
     scales[2] = ldexpf(1.0f, -el - eu);
@@ -492,7 +493,8 @@ TcWs carve_ws(void *ws, int M, int N, int Kpad, int split, int esz) {
 // tiles on or below the diagonal.
 template <typename H, uint32_t FMT, int SPLIT>
 cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22, long lda,
-                void *ws, MpDevStatus *st, cudaStream_t s, bool nt = false, int lower = 0) {
+                void *ws, MpDevStatus *st, cudaStream_t s, bool nt = false, int lower = 0,
+                const unsigned *umax_pre = nullptr) {
     constexpr int BKE = bk_elems<FMT>();
     constexpr bool SCALED = scaled<FMT, SPLIT>();
     const int Kpad = (K + BKE - 1) / BKE * BKE;
@@ -518,17 +520,20 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
         }
         e = cudaMemsetAsync(w.umax, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
-        mp_note_launch();
-        if (nt)
-            absmax_kernel<<<1216, 256, 0, s>>>(N, K, U12, ldu, w.umax);
-        else
-            absmax_kernel<<<1216, 256, 0, s>>>(K, N, U12, ldu, w.umax);
+        if (!umax_pre) {  // else max|U12| was taken while U12 was formed
+            mp_note_launch();
+            if (nt)
+                absmax_kernel<<<1216, 256, 0, s>>>(N, K, U12, ldu, w.umax);
+            else
+                absmax_kernel<<<1216, 256, 0, s>>>(K, N, U12, ldu, w.umax);
+        }
         if (lmax) {
             mp_note_launch();
             absmax_kernel<<<1216, 256, 0, s>>>(M, K, L21, ldl, w.umax + 1);
         }
         mp_note_launch();
-        split_scales_kernel<<<1, 1, 0, s>>>(w.umax, w.scales, lmax ? 1 : 0, FMT == 2 ? 8 : 14);
+        split_scales_kernel<<<1, 1, 0, s>>>(umax_pre ? umax_pre : w.umax, w.umax + 1, w.scales, lmax ? 1 : 0,
+                                            FMT == 2 ? 8 : 14);
     }
     {
         if (nt) {
@@ -578,12 +583,17 @@ size_t tc_workspace_bytes(int n, int nb, int prec) {
 }
 
 cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, long ldl, const float *U12,
-                               long ldu, float *A22, long lda, void *ws, MpDevStatus *st, cudaStream_t s) {
+                               long ldu, float *A22, long lda, void *ws, MpDevStatus *st, cudaStream_t s,
+                               const unsigned *umax_pre) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    if (prec == MP_PREC_BF16) return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
-    if (prec == MP_PREC_FP16) return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
-    if (prec == MP_PREC_FP16X3) return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
-    if (prec == MP_PREC_E4M3) return run<__nv_fp8_e4m3, 2, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s);
+    if (prec == MP_PREC_BF16)
+        return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
+    if (prec == MP_PREC_FP16)
+        return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
+    if (prec == MP_PREC_FP16X3)
+        return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
+    if (prec == MP_PREC_E4M3)
+        return run<__nv_fp8_e4m3, 2, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
     return cudaErrorInvalidValue;
 }
 
