@@ -24,7 +24,9 @@
  *
  * Parity status per routine (pins live in the tests):
  *   getrf/getrs/potrf/potrs (FP64, FP32) : pinned (exact rationals, closed forms)
- *   residual, residual_dot2             : pinned (exact rationals)
+ *   getrs_trans                         : pinned (exact rational solve of A^T x = b
+ *                                         on matrices that must pivot)
+ *   residual, residual_dot2, matvec_dot2 : pinned (exact rationals, cancelling sums)
  *   norm_inf, bwd_err                   : pinned (exact rationals)
  *   gesv_ir, posv_ir                    : pinned (special cases, closed forms,
  *                                         Datta iteration-count prediction)

@@ -83,6 +83,63 @@ def test_getrs_matches_exact_solve(orc, n):
         assert abs(x[i] - float(x_ex[i])) <= 10 * kappa * U64 * max(abs(float(v)) for v in x_ex)
 
 
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+@pytest.mark.parametrize("seed", range(4))
+def test_getrs_trans_matches_exact_transposed_solve(orc, n, seed):
+    """A^T x = b solved with the LU factors of A (U^T L^T P x = b: U^T forward,
+    L^T backward, then the row exchanges undone in reverse order) against the
+    exact rational solve of the transposed system.  The diagonal of A is zeroed
+    so that partial pivoting must exchange rows; several exchanges that do not
+    commute make the order of the final permutation visible."""
+    A = inputs.small_integer_matrix(n, seed=300 + 10 * n + seed, lo=-99, hi=99)
+    A[np.diag_indices(n)] = 0.0
+    Af = exact.to_frac_matrix(A.tolist())
+    if _exact_has_pivot_tie(Af):
+        pytest.skip("pivot choice not unique at this tolerance")
+    At = [[Af[j][i] for j in range(n)] for i in range(n)]
+    b = np.array([(-1.0) ** i * (i + 2) for i in range(n)])
+    x_ex = exact.solve(At, [Fraction(v) for v in b])
+    kappa = float(exact.norm_inf(At) * exact.norm_inf(exact.inverse(At)))
+    LU, piv, info = orc.getrf(A)
+    assert info == 0
+    assert any(p != k + 1 for k, p in enumerate(piv))
+    x = orc.getrs_trans(LU, piv, b)
+    xm = max(abs(float(v)) for v in x_ex)
+    for i in range(n):
+        assert abs(x[i] - float(x_ex[i])) <= 10 * kappa * U64 * xm, (i, x[i], float(x_ex[i]))
+    # several right-hand sides are independent columns
+    B2 = np.stack([b, -2.0 * b[::-1]], axis=1)
+    X2 = orc.getrs_trans(LU, piv, B2)
+    x2_ex = exact.solve(At, [Fraction(v) for v in B2[:, 1]])
+    assert np.array_equal(X2[:, 0], x)
+    for i in range(n):
+        assert abs(X2[i, 1] - float(x2_ex[i])) <= 10 * kappa * U64 * max(abs(float(v)) for v in x2_ex)
+
+
+@pytest.mark.parametrize("n", [3, 6, 8])
+def test_matvec_dot2_against_exact(orc, n):
+    """b = A x with the compensated Dot2 product is the exact rational A x
+    rounded once, up to the Dot2 bound, on products that cancel almost
+    completely (the last column of A is chosen so that A x is tiny next to
+    |A| |x|, where a plain FP64 sum would be wrong in most digits)."""
+    rng = np.random.default_rng(1000 + n)
+    A = rng.standard_normal((n, 2 * n))[:, :n].copy(order="F")
+    X = rng.standard_normal((n, 2))
+    A[:, -1] = -(A[:, :-1] @ X[:-1, 0]) / X[-1, 0] + rng.standard_normal(n) * 1e-13
+    B = orc.matvec_dot2(A, X)
+    Af = exact.to_frac_matrix(A.tolist())
+    absterm = np.abs(A) @ np.abs(X)
+    for c in range(2):
+        xc = [Fraction(v) for v in X[:, c]]
+        for i in range(n):
+            e = float(sum(Af[i][j] * xc[j] for j in range(n)))
+            assert abs(B[i, c] - e) <= U64 * abs(e) + 4 * (n + 1) ** 2 * U64 ** 2 * absterm[i, c], (c, i)
+    # the cancelling column is the one that separates Dot2 from a plain sum
+    assert np.max(np.abs(B[:, 0]) / absterm[:, 0]) < 1e-9
+    b1 = orc.matvec_dot2(A, X[:, 1])
+    assert b1.shape == (n,) and np.array_equal(b1, B[:, 1])
+
+
 @pytest.mark.parametrize("n", [3, 5, 8])
 @pytest.mark.parametrize("seed", range(4))
 def test_refined_solution_matches_exact_solve(orc, n, seed):
