@@ -19,7 +19,15 @@ workloads instead (one JSON line each, not the headline).
                with CUDA events on its own stream by the library's profiler
                during the timed steps.
   cpu_baseline = the CPU oracle (plain C, Algorithm 1 with an FP32 factor)
-               timed on this host's cores on a smaller n of the same recipe.
+               timed on this host's cores, once, at the headline n (about 80 s).
+  vs_baseline = value over the plain FP64 LU solve of the same system on the
+               same GPU (cuSOLVER getrf + getrs through torch); "fp64_lu" also
+               carries the library's own FP64 path (prec=fp64).
+  configs    = one row per workload configuration and factor precision
+               (dense n=1024; the n=16384 precision sweep; prescribed-kappa
+               general and SPD systems at n=4096; the batch of 4096 systems;
+               the adjoint solve), each with time, rate, corrections, flags
+               and errors.  --no-configs / --no-fp64 / --no-cpu skip parts.
 
 --impl reference times the CPU oracle arm instead (the only reference that
 exists for this method is the paper; its CPU restatement is the oracle).
@@ -88,7 +96,10 @@ def class_rooflines(prof, peaks, prec, n, nrhs):
             bound, unit, peak, src = "alu", "TFLOP/s", fp32, "sm_max_mhz x 152 SM x 128 lanes x 2"
             achieved = work / (ms * 1e-3) / 1e12
         elif cls == "residual":
-            bound, unit, peak, src = "alu", "TFLOP/s", FP64_NOMINAL_TFLOPS, "nominal FP64"
+            if peaks.get("fp64_tflops"):
+                bound, unit, peak, src = "alu", "TFLOP/s", peaks["fp64_tflops"], "measured FP64 (cuBLAS DGEMM)"
+            else:
+                bound, unit, peak, src = "alu", "TFLOP/s", FP64_NOMINAL_TFLOPS, "nominal FP64 (not measured)"
             achieved = nl * 2.0 * n * n * nrhs / (ms * 1e-3) / 1e12
         else:
             bound, unit, peak, src = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0), peaks["_source"]
@@ -294,6 +305,241 @@ def run_secondary(args):
     return 0
 
 
+# kernel class -> (kernel name, source file) for the traffic record
+CLASS_KERNEL = {"panel": ("panel_getf2_kernel", "paper_0808_2794_gb300/csrc/panel.cu"),
+                "panelgemm": ("leaf_update_persistent_kernel", "paper_0808_2794_gb300/csrc/blas3.cu"),
+                "update": ("tc_update_kernel", "paper_0808_2794_gb300/csrc/tc_gemm.cu"),
+                "trsv": ("trsv_persistent_kernel", "paper_0808_2794_gb300/csrc/trsv.cu"),
+                "residual": ("residual_partial_kernel", "paper_0808_2794_gb300/csrc/refine.cu")}
+
+
+def source_sha16(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(cls):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of the class's kernel, from the ncu summary table in profiles/traffic.md,
+    or None when there is no record or the kernel's source file has changed
+    since the counters were taken (the table stores the file's hash)."""
+    if cls not in CLASS_KERNEL:
+        return None, None
+    kern, src = CLASS_KERNEL[cls]
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None, None
+    sha = source_sha16(src)
+    with open(path) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 7 and cells[0] == cls and cells[1] == kern:
+                try:
+                    bytes_per_launch = float(cells[6])
+                except ValueError:
+                    continue
+                if cells[3] != sha:
+                    return None, f"{kern}: source changed since the capture ({cells[3]} != {sha})"
+                return bytes_per_launch, f"{kern}: {cells[4]} (profiles/traffic.md)"
+    return None, None
+
+
+def _cuda_ms(torch, fn, reps):
+    """Runs fn() reps times, each bracketed by CUDA events on the current
+    stream with a synchronize on both sides; returns (median ms, last result)."""
+    stream = torch.cuda.current_stream()
+    times, out = [], None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times)), out
+
+
+def fp64_peak_probe(torch):
+    """Measured FP64 ceiling of this GPU: cuBLAS DGEMM (torch.matmul on
+    float64 CUDA tensors) at 4096^3, best of 3 after 2 warm-ups.  A plain
+    library GEMM, used only as the denominator of the FP64-pipe-bound
+    residual, the way the bf16 peak comes from a cuBLAS GEMM."""
+    n = 4096
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    _cuda_ms(torch, lambda: torch.matmul(a, b), 2)
+    best = min(_cuda_ms(torch, lambda: torch.matmul(a, b), 1)[0] for _ in range(3))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def _bwd(torch, solver, Ad, X, Bd):
+    """Normwise backward error max_c ||b - A x||inf / (||A||inf ||x||inf + ||b||inf)
+    with the FP64 residual entry point of the library."""
+    n = Ad.shape[0]
+    X2, B2 = X.reshape(n, -1), Bd.reshape(n, -1)
+    R = solver.residual(Ad, X2, B2)
+    anorm = float(torch.linalg.matrix_norm(Ad, ord=float("inf")))
+    num = R.abs().amax(dim=0)
+    den = anorm * X2.abs().amax(dim=0) + B2.abs().amax(dim=0)
+    return float((num / den).max())
+
+
+def fp64_lu_baselines(torch, solver, Ad, Bd, n, reps=2):
+    """The metric's comparator: the plain FP64 LU solve on this GPU.
+    (1) cuSOLVER getrf + getrs through torch.linalg.lu_factor / lu_solve with
+    the cuSOLVER backend selected; (2) this library's own FP64 path
+    (prec=fp64: FP64 factors and solves, no low precision).  One untimed run
+    each, then `reps` timed runs (median)."""
+    out = {}
+    flops = 2.0 * n ** 3 / 3.0
+    prev = torch.backends.cuda.preferred_linalg_library()
+    try:
+        torch.backends.cuda.preferred_linalg_library("cusolver")
+
+        def cus():
+            LU, piv = torch.linalg.lu_factor(Ad)
+            return torch.linalg.lu_solve(LU, piv, Bd.reshape(n, -1))
+        cus()
+        ms, X = _cuda_ms(torch, cus, reps)
+        env = {k: os.environ[k] for k in ("CUBLAS_EMULATION_STRATEGY", "CUBLAS_EMULATE_DOUBLE_PRECISION",
+                                          "CUSOLVER_EMULATION_STRATEGY") if k in os.environ}
+        out["cusolver"] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "bwd_err": _bwd(torch, solver, Ad, X, Bd),
+                           "call": "torch.linalg.lu_factor + lu_solve, preferred_linalg_library('cusolver')",
+                           "math_mode": "default (FP64 arithmetic; no emulation requested)" if not env else env}
+        del X
+    except Exception as ex:  # recorded, the headline still prints
+        out["cusolver"] = {"error": repr(ex)[:200]}
+    finally:
+        torch.backends.cuda.preferred_linalg_library(prev)
+    torch.cuda.empty_cache()
+    try:
+        import ctypes
+        lib = solver.load()
+        o = solver.default_opts(prec="fp64")
+        work = solver.workspace(lib.mp_gesv_workspace_bytes(n, 1, ctypes.byref(o)))
+        fn = lambda: solver.gesv(Ad, Bd, prec="fp64", work=work)
+        fn()
+        ms, (X, _, st) = _cuda_ms(torch, fn, reps)
+        out["own_fp64"] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "bwd_err": st["bwd_err"],
+                           "iter": st["iter"], "flags": st["flags"],
+                           "call": "mp_gesv with prec=MP_PREC_FP64 (FP64 LU with partial pivoting on the "
+                                   "CUDA cores, FP64 triangular solves, FP64 residual check)"}
+        del work, X
+    except Exception as ex:
+        out["own_fp64"] = {"error": repr(ex)[:200]}
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_report(torch, solver, inputs, Ad, Bd, Xtrue, n, fp64_ms):
+    """One row per configuration and rung of the workloads the solver is
+    specified for: dense FP32 + IR at n=1024; the precision sweep at the
+    headline n (fp32, fp16x3, bf16, fp16, e4m3; refinement 'auto' continues
+    with GMRES where classical refinement stalls); general and SPD systems of
+    prescribed condition number at n=4096, nrhs=4 (fp16 factors, classical vs
+    GMRES); the batch of 4096 uneven systems (fp32, bf16); the adjoint solve
+    at n=2048, nrhs=8.  Every row records time, rate, corrections, flags and
+    errors; a row whose solve raised records the error instead."""
+    import ctypes
+    lib = solver.load()
+    rows = []
+
+    def solve_row(name, A_d, B_d, X_true, prec, refine, spd=False, reps=3):
+        nn = A_d.shape[0]
+        fn = (lambda: solver.posv(A_d, B_d, prec=prec, refine=refine)) if spd else \
+             (lambda: solver.gesv(A_d, B_d, prec=prec, refine=refine))
+        try:
+            ms0, res = _cuda_ms(torch, fn, 1)
+            if ms0 < 500:
+                ms, res = _cuda_ms(torch, fn, reps)
+            else:
+                ms = ms0
+            X, st = (res[0], res[1]) if spd else (res[0], res[2])
+            flops = nn ** 3 / 3.0 if spd else 2.0 * nn ** 3 / 3.0
+            Xt = torch.from_numpy(np.asarray(X_true)).reshape(nn, -1)
+            fwd = float((X.reshape(nn, -1).cpu() - Xt).abs().max() / Xt.abs().max())
+            row = {"config": name, "prec": prec, "refine": refine, "ms": ms,
+                   "gflops": flops / (ms * 1e-3) / 1e9, "iter": st["iter"], "flags": st["flags"],
+                   "bwd_err": st["bwd_err"], "fwd_err_vs_xtrue": fwd,
+                   "n_precond": st.get("n_precond")}
+        except Exception as ex:
+            row = {"config": name, "prec": prec, "refine": refine, "error": repr(ex)[:200]}
+        rows.append(row)
+        torch.cuda.empty_cache()
+        return row
+
+    # config 1: dense FP32 LU + FP64 refinement, n = 1024
+    A1, B1, X1 = inputs.dense_system(1024, seed=0)
+    A1d, B1d = torch.from_numpy(A1).cuda(), torch.from_numpy(B1).cuda()
+    solve_row("1: dense N(0,1), n=1024, nrhs=1", A1d, B1d, X1, "fp32", "classical", reps=5)
+    del A1d, B1d
+    # config 2: precision sweep at the headline size
+    for prec, refine in (("fp32", "classical"), ("fp16x3", "classical"), ("bf16", "auto"),
+                         ("fp16", "auto"), ("e4m3", "auto")):
+        r = solve_row(f"2: dense N(0,1), n={n}, nrhs=1", Ad, Bd, Xtrue, prec, refine, reps=2)
+        if fp64_ms and "ms" in r:
+            r["speedup_vs_fp64_lu"] = fp64_ms / r["ms"]
+    # config 3: prescribed condition number, n = 4096, nrhs = 4, fp16 factors
+    for spd in (False, True):
+        for kappa, A3, B3, X3 in inputs.conditioned_family(4096, (1e2, 1e4, 1e6, 1e8), nrhs=4, spd=spd, seed=0):
+            A3d, B3d = torch.from_numpy(A3).cuda(), torch.from_numpy(B3).cuda()
+            kind = "SPD U diag(s) U^T, Cholesky" if spd else "general U diag(s) V^T, LU"
+            for refine in ("classical", "gmres"):
+                solve_row(f"3: {kind}, kappa={kappa:g}, n=4096, nrhs=4", A3d, B3d, X3, "fp16", refine,
+                          spd=spd, reps=2)
+            del A3d, B3d
+    # config 4: 4096 uneven systems in one launch
+    try:
+        As, Bs, Xs = inputs.batched_systems(count=4096, seed=0)
+        dA = [torch.from_numpy(a).cuda() for a in As]
+        dB = [torch.from_numpy(b).cuda() for b in Bs]
+        flops = sum(2.0 * a.shape[0] ** 3 / 3.0 for a in As)
+        for prec in ("fp32", "bf16"):
+            plan = solver.BatchedPlan(dA, dB, prec=prec)
+            plan.run()
+            ms, _ = _cuda_ms(torch, plan.run, 3)
+            Xo = plan.results()[0]
+            fwd = max(float((x.reshape(x.shape[0], -1).cpu() - torch.from_numpy(xt).reshape(x.shape[0], -1))
+                            .abs().max() / abs(xt).max()) for x, xt in zip(Xo, Xs))
+            rows.append({"config": "4: 4096 systems, n log-uniform [16,512], nrhs 1..4, A = N(0,1) + n I",
+                         "prec": prec, "refine": "classical", "ms": ms, "gflops": flops / (ms * 1e-3) / 1e9,
+                         "iter_max": int(plan.iter.max()), "flags_or": int(np.bitwise_or.reduce(plan.flags)),
+                         "n_fallback": int(np.sum(plan.iter < 0)), "fwd_err_vs_xtrue_max": fwd})
+            del plan
+        del dA, dB
+    except Exception as ex:
+        rows.append({"config": "4: batched", "error": repr(ex)[:200]})
+    torch.cuda.empty_cache()
+    # config 5: adjoint solve, n = 2048, nrhs = 8, fp16 factors
+    try:
+        A5, B5, W5 = inputs.adjoint_problem(2048, 8, seed=0)
+        A5d, B5d, W5d = (torch.from_numpy(x).cuda() for x in (A5, B5, W5))
+        o = solver.default_opts(prec="fp16")
+        work = solver.workspace(lib.mp_gesv_workspace_bytes(2048, 8, ctypes.byref(o)))
+        adj = solver.workspace(lib.mp_gesv_adjoint_workspace_bytes(2048, ctypes.byref(o)))
+
+        def fwd_bwd():
+            X, _, st = solver.gesv(A5d, B5d, prec="fp16", work=work)
+            Abar, Bbar, sta = solver.gesv_adjoint(A5d, X, W5d, work, prec="fp16", adj_work=adj)
+            return st, sta
+        fwd_bwd()
+        ms, (st, sta) = _cuda_ms(torch, fwd_bwd, 3)
+        rows.append({"config": "5: adjoint, A = N(0,1) + sqrt(n) I, n=2048, nrhs=8", "prec": "fp16",
+                     "refine": "classical", "ms_forward_plus_adjoint": ms, "iter": st["iter"],
+                     "iter_adjoint": sta["iter"], "flags": st["flags"], "flags_adjoint": sta["flags"],
+                     "bwd_err": st["bwd_err"], "bwd_err_adjoint": sta["bwd_err"]})
+        del work, adj
+    except Exception as ex:
+        rows.append({"config": "5: adjoint", "error": repr(ex)[:200]})
+    torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,9 +556,11 @@ def main():
     ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--ref-n", type=int, default=4096)
-    ap.add_argument("--cpu-n", type=int, default=8192)
+    ap.add_argument("--cpu-n", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 LU comparator")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-config report")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -395,24 +643,44 @@ def main():
 
     # roofline of the dominant kernel class
     peaks = load_peaks()
+    if rank == 0 and not args.no_fp64:
+        try:
+            peaks["fp64_tflops"] = fp64_peak_probe(torch)
+        except Exception:
+            pass
     ms_d, nl_d, work_d = prof[dom]
     if dom in ("update", "trsm", "panelgemm", "panel"):
-        tensor = dom == "update" and args.prec in ("bf16", "fp16", "fp16x3")
+        tensor = dom == "update" and args.prec in ("bf16", "fp16", "fp16x3", "e4m3")
         if tensor:
             bound, unit, peak = "tensor", "TFLOP/s", peaks.get("bf16_tflops_sustained", 1700.0)
+            psrc = f"bf16_tflops_sustained ({peaks['_source']}, cuBLAS bf16 GEMM)"
+            if args.prec == "fp16x3":
+                work_d = 3.0 * work_d  # three products per k-step on the tensor pipe
+            elif args.prec == "e4m3":
+                peak = 2.0 * peak
+                psrc += " x 2 (fp8 nominal ratio)"
         else:
             smx = peaks.get("sm_max_mhz", 2070.0)
             bound, unit = "alu", "TFLOP/s"
             peak = 152 * 128 * 2 * smx * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+            psrc = "derived: 152 SM x 128 FP32 lanes x 2 flops x sm_max_mhz"
         achieved = work_d / (ms_d * 1e-3) / 1e12 if ms_d > 0 else 0.0
+    elif dom == "residual":
+        bound, unit = "alu", "TFLOP/s"
+        peak = peaks.get("fp64_tflops") or FP64_NOMINAL_TFLOPS
+        psrc = "measured FP64 (cuBLAS DGEMM)" if peaks.get("fp64_tflops") else "nominal FP64 (not measured)"
+        achieved = nl_d * 2.0 * n * n * nrhs / (ms_d * 1e-3) / 1e12 if ms_d > 0 else 0.0
     else:
         bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
+        psrc = f"hbm_gbs ({peaks['_source']})"
         achieved = work_d / (ms_d * 1e-3) / 1e9 if ms_d > 0 else 0.0
     share = ms_d / (ms_total) if ms_total > 0 else 0.0
+    traffic, traffic_src = recorded_traffic(dom)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "kernel": dom, "share_of_step": share, "launches_timed": nl_d,
-                "peak_source": peaks["_source"]}
+                "peak_source": psrc}
     breakdown = {c: round(v[0] / max(1, 1), 3) for c, v in prof0.items()}
     by_class = class_rooflines(prof0, peaks, args.prec, n, nrhs)
 
@@ -448,6 +716,19 @@ def main():
                "d2h_bytes_per_step": 8 * n * nrhs + 4 * n, "ms_per_step": e2e_ms}
         del wh
 
+    # the metric's comparator (plain FP64 LU on this GPU) and the per-config report
+    fp64 = None
+    configs = None
+    if rank == 0 and not args.no_fp64:
+        fp64 = fp64_lu_baselines(torch, solver, Ad, Bd, n)
+    cus_ms = (fp64 or {}).get("cusolver", {}).get("ms")
+    vs_baseline = None
+    if cus_ms:
+        # replicas: N GPUs run N plain FP64 solves in the time of one
+        vs_baseline = value / (ws * (2.0 * n ** 3 / 3.0) / (cus_ms * 1e-3) / 1e9)
+    if rank == 0 and not args.no_configs:
+        configs = config_report(torch, solver, inputs, Ad, Bd, Xtrue, n, cus_ms)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, cores, dt, r = cpu_oracle_rate(args.cpu_n)
@@ -460,7 +741,10 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "weak", "vs_baseline": vs_baseline,
+            "vs_baseline_of": "plain FP64 LU solve on this GPU (cuSOLVER getrf + getrs via torch), "
+                              "same n and inputs: value / (n_gpus x its rate)",
+            "fp64_lu": fp64, "fp64_peak_tflops": peaks.get("fp64_tflops"),
             "dtype": f"{args.prec}-factor/f64-refine", "data": "synthetic",
             "config": {"workload": f"dense LU solve, A~N(0,1), x~U[-1,1], n={n}, nrhs={nrhs}",
                        "n": n, "nrhs": nrhs, "prec": args.prec, "nb_outer": args.nb,
@@ -474,6 +758,7 @@ def main():
                       "ms_refine": last["ms_refine"], "ms_fallback": last["ms_fallback"]},
             "kernel_ms_first_warmup": breakdown,
             "rooflines_by_class": by_class,
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

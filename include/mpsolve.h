@@ -58,9 +58,15 @@ typedef enum {
                            accumulation: about FP32 accuracy at fp16 tensor-core speed */
     MP_PREC_BF16 = 2,   /* trailing-update operands rounded to bfloat16, FP32 accumulation */
     MP_PREC_FP16 = 3,   /* trailing-update operands rounded to binary16, FP32 accumulation */
-    MP_PREC_E4M3 = 4    /* trailing-update operands scaled by a power of two per operand and
+    MP_PREC_E4M3 = 4,   /* trailing-update operands scaled by a power of two per operand and
                            rounded to FP8 E4M3 (round to nearest even, saturating at 448),
                            FP32 accumulation (tcgen05 kind::f8f6f4) */
+    MP_PREC_FP64 = 5    /* no low precision: the plain double-precision solve that the paper
+                           measures its speedups against (Section 3, Table 3: DGETRF + DGETRS,
+                           DPOTRF + DPOTRS), FP64 factors on the GPU, x_0 from them and the same
+                           acceptance test (FP64 corrections if x_0 misses it).  mp_gesv and
+                           mp_posv only; the FALLBACK flag is never set and iter counts the FP64
+                           corrections.  The other entry points reject it. */
 } mp_prec;
 
 /* Refinement scheme. */
@@ -196,11 +202,11 @@ MP_API int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const dou
                            const mp_opts *opts, mp_stats *stats, void *stream);
 
 /* Allocation-free variant of mp_gesv (the paper has no counterpart; this is
- * a deployment convenience).  Some callers may not call cudaMalloc: code that
- * runs while a CUDA graph is being captured, services that fix their device
- * memory at start-up and forbid allocation afterwards (an allocation can
- * synchronize the device and can fail under memory pressure), and plug-ins
- * whose host framework owns every device allocation.  This entry point takes
+ * a deployment convenience).  Some callers may not call cudaMalloc: services
+ * that fix their device memory at start-up and forbid allocation afterwards
+ * (an allocation can synchronize the device and can fail under memory
+ * pressure), and plug-ins whose host framework owns every device allocation
+ * and hands them no allocator.  This entry point takes
  * its scratch from a static device array of MP_NOALLOC_SCRATCH_BYTES that is
  * part of the library image: every GPU that loads the library holds that
  * memory until the process exits.  The caller still passes A, B, X and ipiv
@@ -209,7 +215,9 @@ MP_API int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const dou
  *     return -1 with an explanatory mp_last_error().
  *   - The first call on a device looks up the array's device address and
  *     creates the internal streams (with that device current); make that
- *     first call before any stream capture.
+ *     first call before any stream capture.  The address is kept for the
+ *     life of the process: do not call this entry point again on a device
+ *     after cudaDeviceReset (or any other teardown of its primary context).
  *   - Every call on a device shares the one array and it keeps the previous
  *     call's contents; the solver re-initializes everything it needs.  Calls
  *     that overlap on the GPU (different streams or host threads) race on the

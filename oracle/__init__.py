@@ -81,6 +81,7 @@ def _load():
                 "or_posv_ir": (I, [I, I, P, I, P, I, P, I, I, I, D, D, I, P, P, P]),
                 "or_kappa_inf": (D, [I, P, I]),
                 "or_kappa_1_est": (D, [I, P, I]),
+                "or_dinvnorm1_est_lu": (D, [I, P, I, P, I]),
                 "or_round_bf16": (D, [D]),
                 "or_round_fp16": (D, [D]),
                 "or_round_e4m3": (D, [D]),
@@ -289,6 +290,16 @@ def kappa_inf(A) -> float:
     lib = _load()
     Af = _f(A, np.float64)
     return float(lib.or_kappa_inf(Af.shape[0], _p(Af), max(Af.shape[0], 1)))
+
+
+def kappa_inf_est_lu(A, LU, ipiv) -> float:
+    """kappa_inf(A) estimate ||A||_inf * est(||A^{-1}||_inf) from existing FP64
+    LU factors of A (Hager-Higham on A^{-T}; a lower bound)."""
+    lib = _load()
+    F = _f(LU, np.float64)
+    piv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    n = F.shape[0]
+    return norm_inf(A) * float(lib.or_dinvnorm1_est_lu(n, _p(F), max(n, 1), _p(piv), 1))
 
 
 def kappa_1_est(A) -> float:

@@ -30,7 +30,8 @@
  *   norm_inf, bwd_err                   : pinned (exact rationals)
  *   gesv_ir, posv_ir                    : pinned (special cases, closed forms,
  *                                         Datta iteration-count prediction)
- *   kappa_inf_exact, kappa_1_est        : pinned (Hilbert / tridiagonal closed forms)
+ *   kappa_inf_exact, kappa_1_est,       : pinned (Hilbert / tridiagonal closed forms;
+ *   dinvnorm1_est_lu                      lower bound within 10x of the exact norm)
  *   gmres_ir                            : pinned (special cases, exact solve bound)
  *   round_bf16/fp16/e4m3                : pinned (enumerated representable values)
  */
@@ -793,12 +794,57 @@ double or_kappa_inf(int n, const double *A, int lda) {
  * A^T using existing FP64 LU factors, and returns kappa_1 estimate
  * = ||A||_1 * est (a lower bound of the true kappa_1).  kappa_inf(A) =
  * kappa_1(A^T), so passing A^T estimates kappa_inf. */
+/* The estimate of ||A^{-1}||_1 itself, from existing FP64 LU factors F,
+ * ipiv of A.  trans = 1 estimates ||A^{-T}||_1 = ||A^{-1}||_inf instead (the
+ * solves with A and A^T swap roles), so kappa_inf(A) can be estimated from
+ * the factors of A without factoring A^T. */
+double or_dinvnorm1_est_lu(int n, const double *F, int ldf, const int *ipiv, int trans) {
+    double *x = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *z = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) x[i] = 1.0 / n;
+    double est = 0.0;
+    for (int it = 1; it <= 5; ++it) {
+        /* y = B x with B = A^{-1} (trans = 0) or A^{-T} (trans = 1) */
+        for (int i = 0; i < n; ++i) y[i] = x[i];
+        if (trans) or_dgetrs_trans(n, 1, F, ldf, ipiv, y, n);
+        else or_dgetrs(n, 1, F, ldf, ipiv, y, n);
+        double g = 0.0;
+        for (int i = 0; i < n; ++i) g += fabs(y[i]);
+        if (it > 1 && g <= est) break;
+        est = g;
+        /* z = B^T sign(y) */
+        for (int i = 0; i < n; ++i) z[i] = (y[i] >= 0.0) ? 1.0 : -1.0;
+        if (trans) or_dgetrs(n, 1, F, ldf, ipiv, z, n);
+        else or_dgetrs_trans(n, 1, F, ldf, ipiv, z, n);
+        int j = 0;
+        double zmax = fabs(z[0]), ztx = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (fabs(z[i]) > zmax) { zmax = fabs(z[i]); j = i; }
+            ztx += z[i] * x[i];
+        }
+        if (it > 1 && zmax <= ztx) break;
+        for (int i = 0; i < n; ++i) x[i] = 0.0;
+        x[j] = 1.0;
+    }
+    /* Higham's alternating-sign safeguard vector */
+    for (int i = 0; i < n; ++i)
+        y[i] = ((i % 2) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n > 1 ? n - 1 : 1));
+    if (trans) or_dgetrs_trans(n, 1, F, ldf, ipiv, y, n);
+    else or_dgetrs(n, 1, F, ldf, ipiv, y, n);
+    double alt = 0.0;
+    for (int i = 0; i < n; ++i) alt += fabs(y[i]);
+    alt = 2.0 * alt / (3.0 * n);
+    free(x);
+    free(y);
+    free(z);
+    return fmax(est, alt);
+}
+
 double or_kappa_1_est(int n, const double *A, int lda) {
     size_t nn = (size_t)n * (size_t)n;
     double *F = (double *)malloc(sizeof(double) * (nn ? nn : 1));
     int *ipiv = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    double *x = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) F[IDX(i, j, n)] = A[IDX(i, j, lda)];
     double anorm1 = 0.0;
@@ -808,45 +854,9 @@ double or_kappa_1_est(int n, const double *A, int lda) {
         anorm1 = fmax(anorm1, s);
     }
     double est = INFINITY;
-    double *z = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    if (or_dgetrf(n, F, n, ipiv) == 0) {
-        for (int i = 0; i < n; ++i) x[i] = 1.0 / n;
-        est = 0.0;
-        for (int it = 1; it <= 5; ++it) {
-            /* y = A^{-1} x */
-            for (int i = 0; i < n; ++i) y[i] = x[i];
-            or_dgetrs(n, 1, F, n, ipiv, y, n);
-            double g = 0.0;
-            for (int i = 0; i < n; ++i) g += fabs(y[i]);
-            if (it > 1 && g <= est) break;
-            est = g;
-            /* z = A^{-T} sign(y) */
-            for (int i = 0; i < n; ++i) z[i] = (y[i] >= 0.0) ? 1.0 : -1.0;
-            or_dgetrs_trans(n, 1, F, n, ipiv, z, n);
-            int j = 0;
-            double zmax = fabs(z[0]), ztx = 0.0;
-            for (int i = 0; i < n; ++i) {
-                if (fabs(z[i]) > zmax) { zmax = fabs(z[i]); j = i; }
-                ztx += z[i] * x[i];
-            }
-            if (it > 1 && zmax <= ztx) break;
-            for (int i = 0; i < n; ++i) x[i] = 0.0;
-            x[j] = 1.0;
-        }
-        /* Higham's alternating-sign safeguard vector */
-        for (int i = 0; i < n; ++i)
-            y[i] = ((i % 2) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n > 1 ? n - 1 : 1));
-        or_dgetrs(n, 1, F, n, ipiv, y, n);
-        double alt = 0.0;
-        for (int i = 0; i < n; ++i) alt += fabs(y[i]);
-        alt = 2.0 * alt / (3.0 * n);
-        est = fmax(est, alt);
-    }
-    free(z);
+    if (or_dgetrf(n, F, n, ipiv) == 0) est = or_dinvnorm1_est_lu(n, F, n, ipiv, 0);
     free(F);
     free(ipiv);
-    free(x);
-    free(y);
     return anorm1 * est;
 }
 

@@ -6,7 +6,9 @@
 // library holds its MP_NOALLOC_SCRATCH_BYTES until the process exits.  Host
 // code only sees a host-side stand-in under the array's name; the device
 // address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and cached here.
+// device current) and cached here for the life of the process; a device reset
+// would reload the module and leave the cached address stale, so the entry
+// point is documented as not usable after cudaDeviceReset.
 #include <cstdio>
 #include <mutex>
 

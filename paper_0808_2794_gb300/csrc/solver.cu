@@ -194,7 +194,7 @@ int outer_nb(int n, const mp_opts &o) {
     // wider panels make the tensor-core trailing update more efficient, but
     // the leaf pipeline's bulk launches (which also form U12 left-looking,
     // K up to the panel width) then outgrow the panel kernels they overlap
-    if (o.prec == MP_PREC_FP32) return n >= 4096 ? 256 : 128;
+    if (o.prec == MP_PREC_FP32 || o.prec == MP_PREC_FP64) return n >= 4096 ? 256 : 128;
     return n >= 8192 ? 384 : 256;
 }
 
@@ -214,6 +214,9 @@ size_t carve(size_t &off, size_t bytes) {
     off += bytes;
     return at;
 }
+
+// Room for FP64 factors is needed by the fallback and by the plain FP64 solve.
+bool fp64_space_of(const mp_opts &o) { return o.allow_fallback != 0 || o.prec == MP_PREC_FP64; }
 
 // fp64_space: room for the FP64 fallback (W, inverses, vectors sized for double)
 Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym = false) {
@@ -245,8 +248,9 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.Z = carve(off, el * (size_t)n * rhs);
     if (sym) L.ksplit = residual_sym_blocks(n);  // the symmetric residual's partial sums
     L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);
-    L.tc = carve(off, o.prec == MP_PREC_FP32 ? 0
-                                             : std::max(tc_workspace_bytes(n, L.nb, o.prec),
+    L.tc = carve(off, o.prec == MP_PREC_FP32 || o.prec == MP_PREC_FP64
+                          ? 0
+                          : std::max(tc_workspace_bytes(n, L.nb, o.prec),
                                                         tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3)));
     L.linv = carve(off, 3 * 1024 * sizeof(double));  // three leaves' L11^{-1}
     // GMRES: Krylov basis V (m+1 columns), preconditioned vectors Z (m), small vectors
@@ -995,7 +999,7 @@ int refine_gmres(Solve &S, const mp_opts &o, bool from_x, mp_stats *st, bool *co
 }
 
 int validate_opts(const mp_opts &o) {
-    if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_E4M3) return 1;
+    if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_FP64) return 1;
     if (o.itermax < 0 || !(o.tol > 0.0) || o.stall_ratio <= 0.0) return 1;
     if (o.refine < MP_REFINE_CLASSICAL || o.refine > MP_REFINE_AUTO) return 1;
     if (o.refine != MP_REFINE_CLASSICAL &&
@@ -1013,7 +1017,7 @@ extern "C" size_t mp_gesv_workspace_bytes(int n, int nrhs, const mp_opts *opts) 
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
     if (n < 0 || nrhs < 0) return 0;
-    return make_layout(n, nrhs, o, o.allow_fallback != 0).total;
+    return make_layout(n, nrhs, o, fp64_space_of(o)).total;
 }
 
 extern "C" int mp_gesv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
@@ -1047,8 +1051,9 @@ int solve_impl(bool sym, int n, int nrhs, const double *dA, int lda, const doubl
         std::memset(stats, 0, sizeof(*stats));
     }
     if (n == 0 || nrhs == 0) return 0;
-    const bool fb = o.allow_fallback != 0;
-    Layout L = make_layout(n, nrhs, o, fb, sym);
+    const bool plain64 = o.prec == MP_PREC_FP64;  // the plain FP64 solve, no low precision
+    const bool fb = o.allow_fallback != 0 && !plain64;
+    Layout L = make_layout(n, nrhs, o, fp64_space_of(o), sym);
     if (!work) return mp_arg_fail(10 - after, "workspace is NULL");
     if (work_bytes < L.total) return mp_arg_fail(11 - after, "workspace too small");
 
@@ -1068,7 +1073,10 @@ int solve_impl(bool sym, int n, int nrhs, const double *dA, int lda, const doubl
     MP_CUDA_TRY(cudaMemsetAsync(S.sb, 0, sizeof(StatusBlock), s));
     MP_CUDA_TRY(cudaMemsetAsync(at<double>(work, L.rowsum), 0, sizeof(double) * n, s));
     if (reset_sync(S)) return -1000;
-    MP_CUDA_TRY(convert(at<float>(work, L.W)));
+    if (plain64)
+        MP_CUDA_TRY(convert(at<double>(work, L.W)));
+    else
+        MP_CUDA_TRY(convert(at<float>(work, L.W)));
     MP_CUDA_TRY(launch_max_reduce(n, at<double>(work, L.rowsum), &S.sb->st.anorm, s));
     MP_CUDA_TRY(launch_col_absmax(n, nrhs, dB, ldb, S.sb->bnorm, &S.sb->st, s));
     mark(1);
@@ -1077,6 +1085,46 @@ int solve_impl(bool sym, int n, int nrhs, const double *dA, int lda, const doubl
     int info = 0, iters = 0, e;
     bool conv = false;
     uint32_t fflags = 0;
+    if (plain64) {
+        // The plain double-precision solver the paper measures its speedups
+        // against (Section 3: DGETRF + DGETRS, DPOTRF + DPOTRS): FP64 factors,
+        // x_0 from them, and the same acceptance test (corrections, if any,
+        // with the FP64 factors).  The answer is FP64 throughout, so no
+        // fallback flag.
+        int ret = 0;
+        if ((e = factor<double>(S, MP_PREC_FP32, std::min(L.nb, 256), &info, &fflags))) return e;
+        mark(2);
+        flags |= fflags & MP_FLAG_NONFINITE_INPUT;
+        if (info > 0) {
+            ret = info;
+        } else if (!(flags & MP_FLAG_NONFINITE_INPUT)) {
+            if ((e = refine<double>(S, o, o.itermax, false, stats, &conv, &iters, &flags))) return e;
+            if (!conv) flags |= MP_FLAG_NOT_CONVERGED;
+        }
+        mark(3);
+        if (!sym)
+            MP_CUDA_TRY(cudaMemcpyAsync(dipiv, at<int32_t>(work, L.ipiv), sizeof(int32_t) * n,
+                                        cudaMemcpyDeviceToDevice, s));
+        {
+            const int kind = ret != 0 ? kNoFactors : sym ? kCholF64 : kLuF64;
+            MP_CUDA_TRY(cudaMemcpyAsync(&S.sb->factor_kind, &kind, sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        mark(4);
+        MP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (stats) {
+            stats->iter = iters;
+            stats->flags = flags;
+            stats->info = info;
+            if (timing) {
+                cudaEventElapsedTime(&stats->ms_convert, ev[0], ev[1]);
+                cudaEventElapsedTime(&stats->ms_factor, ev[1], ev[2]);
+                cudaEventElapsedTime(&stats->ms_refine, ev[2], ev[3]);
+            }
+        }
+        if (timing)
+            for (auto &x : ev) cudaEventDestroy(x);
+        return ret;
+    }
     if ((e = factor<float>(S, o.prec, L.nb, &info, &fflags))) return e;
     mark(2);
     flags |= fflags & (MP_FLAG_LOWP_BREAKDOWN | MP_FLAG_NONFINITE_INPUT);
@@ -1164,7 +1212,7 @@ extern "C" size_t mp_posv_workspace_bytes(int n, int nrhs, const mp_opts *opts) 
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
     if (n < 0 || nrhs < 0) return 0;
-    return make_layout(n, nrhs, o, o.allow_fallback != 0, true).total;
+    return make_layout(n, nrhs, o, fp64_space_of(o), true).total;
 }
 
 extern "C" int mp_posv(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
@@ -1221,7 +1269,7 @@ extern "C" size_t mp_gesv_adjoint_workspace_bytes(int n, const mp_opts *opts) {
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
     if (n < 0) return 0;
-    return adj_layout(n, o.allow_fallback != 0).total;
+    return adj_layout(n, fp64_space_of(o)).total;
 }
 
 extern "C" int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
@@ -1258,10 +1306,11 @@ extern "C" int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const
         return mp_arg_fail(13, "workspace holds no factors of a finished mp_gesv / mp_posv");
     const bool sym = kind == kCholF32 || kind == kCholF64;
     const bool f64 = kind == kLuF64 || kind == kCholF64;
-    Layout L = make_layout(n, std::max(nrhs, 1), o, o.allow_fallback != 0, sym);
+    Layout L = make_layout(n, std::max(nrhs, 1), o, fp64_space_of(o), sym);
     if (work_bytes < L.total) return mp_arg_fail(14, "workspace too small for (n, nrhs, opts)");
-    if (f64 && !o.allow_fallback) return mp_arg_fail(17, "FP64 factors need allow_fallback = 1 in opts");
-    AdjLayout AL = adj_layout(n, o.allow_fallback != 0);
+    if (f64 && !fp64_space_of(o))
+        return mp_arg_fail(17, "FP64 factors need allow_fallback = 1 (or prec FP64) in opts");
+    AdjLayout AL = adj_layout(n, fp64_space_of(o));
     if (!sym && !adj_work) return mp_arg_fail(15, "adjoint workspace is NULL");
     if (!sym && adj_bytes < AL.total) return mp_arg_fail(16, "adjoint workspace too small");
     if (nrhs == 0) return 0;
@@ -1280,7 +1329,7 @@ extern "C" int mp_gesv_adjoint(int n, int nrhs, const double *dA, int lda, const
     else e = adjoint_solve<float>(S, o, adj_work, AL, stats, &conv, &iters, &flags);
     if (e) return e;
     if (!conv) flags |= MP_FLAG_NOT_CONVERGED;
-    if (f64) flags |= MP_FLAG_FALLBACK;
+    if (f64 && o.prec != MP_PREC_FP64) flags |= MP_FLAG_FALLBACK;
     MP_CUDA_TRY(launch_outer_neg(n, nrhs, dBbar, ldbb, dX, ldx, dAbar, ldab, s));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     if (stats) {
@@ -1423,7 +1472,7 @@ extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp
     if (n > 0 && !dW) return mp_arg_fail(2, "W is NULL");
     if (ldw < mp_factor_ld(n) || ldw % 32) return mp_arg_fail(3, "ldw must be a multiple of 32 >= n");
     if (n > 0 && !dipiv) return mp_arg_fail(4, "ipiv is NULL");
-    if (validate_opts(o)) return mp_arg_fail(5, "invalid options");
+    if (validate_opts(o) || o.prec == MP_PREC_FP64) return mp_arg_fail(5, "invalid options");
     const int nb = outer_nb(n, o);
     StepLayout L = step_layout(n, 1, nb, o.prec);
     if (!work) return mp_arg_fail(6, "workspace is NULL");
@@ -1456,7 +1505,7 @@ extern "C" int mp_potrf_lowp(int n, float *dW, int ldw, const mp_opts *opts, voi
     if (n < 0 || n > 65536) return mp_arg_fail(1, "n out of range [0, 65536]");
     if (n > 0 && !dW) return mp_arg_fail(2, "W is NULL");
     if (ldw < mp_factor_ld(n) || ldw % 32) return mp_arg_fail(3, "ldw must be a multiple of 32 >= n");
-    if (validate_opts(o)) return mp_arg_fail(4, "invalid options");
+    if (validate_opts(o) || o.prec == MP_PREC_FP64) return mp_arg_fail(4, "invalid options");
     const int nb = outer_nb(n, o);
     StepLayout L = step_layout(n, 1, nb, o.prec);
     if (!work) return mp_arg_fail(5, "workspace is NULL");

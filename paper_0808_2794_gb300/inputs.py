@@ -64,6 +64,25 @@ def conditioned_system(n: int, kappa: float, nrhs: int = 1, spd: bool = False, s
     return A, B, X
 
 
+def conditioned_family(n: int, kappas, nrhs: int = 1, spd: bool = False, seed: int = 0):
+    """The systems conditioned_system(n, kappa, nrhs, spd, seed) for every
+    kappa in kappas, with the Haar factors and X_true drawn once: per seed the
+    draws do not depend on kappa, so each (A, B, X) equals the one that
+    conditioned_system returns.  Yields (kappa, A, B, X)."""
+    rng = np.random.default_rng(seed)
+    U = haar_orthogonal(rng, n)
+    V = U if spd else haar_orthogonal(rng, n)
+    X = np.asfortranarray(rng.uniform(-1.0, 1.0, size=(nrhs, n)).T)
+    i = np.arange(n, dtype=np.float64)
+    for kappa in kappas:
+        s = kappa ** (-i / max(n - 1, 1))
+        A = (U * s[None, :]) @ V.T
+        if spd:
+            A = 0.5 * (A + A.T)
+        A = np.asfortranarray(A)
+        yield kappa, A, np.asfortranarray(A @ X), X
+
+
 def batched_systems(count: int = 4096, seed: int = 0, nmin: int = 16, nmax: int = 512,
                     max_nrhs: int = 4):
     """``count`` independent systems, n = round(exp(U[ln nmin, ln nmax])),

@@ -16,7 +16,7 @@ import threading
 
 from . import build as _build
 
-PREC = {"fp32": 0, "fp16x3": 1, "bf16": 2, "fp16": 3, "e4m3": 4}
+PREC = {"fp32": 0, "fp16x3": 1, "bf16": 2, "fp16": 3, "e4m3": 4, "fp64": 5}
 REFINE = {"classical": 0, "gmres": 1, "auto": 2}
 
 FLAG_FALLBACK = 1

@@ -5,6 +5,8 @@ backward error of every column from its compensated (Dot2) FP64 residual over
 the whole matrix, and, where the condition number is known in closed form,
 the forward error.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -43,25 +45,50 @@ def test_dense_lu_n16384_bench_configuration(torch, mp, orc):
     assert np.max(np.abs(X[:, 0] - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-9
 
 
+@pytest.mark.slow
+def test_dense_lu_n16384_against_oracle_fp64(torch, mp, orc):
+    """The benchmark's workload and launch configuration, against the
+    oracle's FP64 solve of the same system: one FP64 LU with partial pivoting
+    on the host cores (about 1.5 minutes on 16 cores), x_or from it with one
+    FP64 correction from the compensated residual, and kappa_inf(A) estimated
+    from the same factors (Hager-Higham, a lower bound).  The GPU solution is
+    within 10 kappa_inf u64 of x_or and every column's backward error, from
+    the oracle's compensated residual, is <= 1e-14."""
+    n = 16384
+    A, B, X_true = inputs.dense_system(n, seed=0)
+    X, piv, st = mp.gesv(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), prec="fp16x3")
+    assert st["flags"] == 0, st
+    X = X.cpu().numpy().reshape(n, 1)
+    assert np.all(orc.bwd_err(A, X, B) <= 1e-14)
+    orc.set_threads(os.cpu_count() or 1)
+    LU, piv_or, info = orc.getrf(A)
+    assert info == 0
+    x0 = orc.getrs(LU, piv_or, B).reshape(n, 1)
+    r = orc.residual(A, x0, B, compensated=True).reshape(n, 1)
+    x_or = x0 + orc.getrs(LU, piv_or, r).reshape(n, 1)
+    kinf = orc.kappa_inf_est_lu(A, LU, piv_or)
+    fwd = np.max(np.abs(X - x_or)) / np.max(np.abs(x_or))
+    assert fwd <= 10 * kinf * U64, (fwd, kinf)
+
+
 @pytest.mark.parametrize("n", [20480, 33024])
-def test_dense_lu_tall_panel_variants(torch, mp, n):
+def test_dense_lu_tall_panel_variants(torch, mp, orc, n):
     """Sizes whose first leaves are taller than 16384 rows (16-column leaves,
     4 rows per thread) and, at n = 33024, taller than 32768 rows (8-column
     leaves, 8 rows per thread), so the panel kernel's taller variants run the
-    whole leaf pipeline.  Too large for the CPU oracle: the backward error
-    comes from the library's FP64 residual (checked against the oracle at the
-    other sizes), the forward error from the known x_true."""
+    whole leaf pipeline.  Too large for an oracle solve: the backward error
+    comes from the oracle's compensated residual over the whole matrix (an
+    O(n^2) pass), the forward error from the known x_true."""
     A, B, X_true = inputs.dense_system(n, seed=3)
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    del A
     X, piv, st = mp.gesv(Ad, Bd)
     assert st["flags"] == 0, st
-    R = mp.residual(Ad, X.reshape(n, 1), Bd.reshape(n, 1))
-    anorm = float(torch.linalg.matrix_norm(Ad, ord=float("inf")))
-    bwd = float(R.abs().max()) / (anorm * float(X.abs().max()) + float(Bd.abs().max()))
-    assert bwd <= 1e-14, (bwd, st)
-    X = X.cpu().numpy().reshape(n)
-    assert np.max(np.abs(X - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-8
+    del Ad
+    X = X.cpu().numpy().reshape(n, 1)
+    orc.set_threads(os.cpu_count() or 1)
+    bwd = orc.bwd_err(A, X, B)
+    assert np.all(bwd <= 1e-14), (bwd, st)
+    assert np.max(np.abs(X[:, 0] - X_true[:, 0])) / np.max(np.abs(X_true)) <= 1e-8
 
 
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e8])

@@ -378,6 +378,33 @@ def test_kappa_estimator_lower_bound(orc):
         assert k_est >= k_true / 10
 
 
+def test_kappa_inf_estimator_from_lu_factors(orc):
+    """The estimate of kappa_inf(A) = ||A||inf ||A^{-1}||inf taken from the
+    LU factors of A (solves with A^T and A in swapped roles) is a lower bound
+    within 10x of the exact value, on dense random matrices and on the
+    tridiagonal Toeplitz matrix, whose inverse is known in closed form; on a
+    non-symmetric matrix it differs from the 1-norm estimate."""
+    for seed in range(3):
+        A, _, _ = inputs.dense_system(80, seed=seed)
+        LU, piv, info = orc.getrf(A)
+        k_true = np.linalg.cond(A, np.inf)
+        k_est = orc.kappa_inf_est_lu(A, LU, piv)
+        assert k_true / 10 <= k_est <= k_true * (1 + 1e-10)
+    n = 40
+    T = np.asfortranarray(2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1))
+    inv = exact.tridiag_inverse_closed_form(n)
+    k_exact = 4.0 * float(exact.norm_inf(inv))
+    LU, piv, _ = orc.getrf(T)
+    k_est = orc.kappa_inf_est_lu(T, LU, piv)
+    assert k_exact / 10 <= k_est <= k_exact * (1 + 1e-10)
+    # a matrix whose 1-norm and inf-norm condition numbers differ widely
+    A = np.asfortranarray(np.eye(30) + np.outer(np.r_[1e3, np.zeros(29)], np.ones(30)))
+    LU, piv, _ = orc.getrf(A)
+    k_inf = np.linalg.cond(A, np.inf)
+    assert k_inf / 10 <= orc.kappa_inf_est_lu(A, LU, piv) <= k_inf * (1 + 1e-10)
+    assert abs(np.linalg.cond(A, 1) - k_inf) > 0.5 * k_inf
+
+
 # ------------------------------------------------------- rounding helpers
 
 def _brute_nearest(x, grid):
