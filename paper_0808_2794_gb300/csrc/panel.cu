@@ -161,7 +161,7 @@ struct PanelSmem {
     Slot<T, NB> rd[2];         // the diagonal row
     Slot<T, NB> stage[2];      // this CTA's outgoing candidate / diagonal row
     uint64_t mbar[2];
-    Cand<T> wkey[NT / 32];
+    Cand<T> wkey[2][NT / 32];  // per-warp candidates, double-buffered by column
     alignas(16) T wsh[NT / 32][NB];  // per-warp shifted pivot row
     // the previous leaf applied on load (PanelPrev; its width is at most NB)
     int redir[NT * RPT];          // local row -> row it takes its values from (INT_MIN: itself)
@@ -380,9 +380,11 @@ panel_getf2_kernel(T *__restrict__ P, long ld, int m, int ncols, int row0, int32
                     if (o.better(c)) c = o;
                 }
             c = warp_best(c);
-            if (lane == 0) sm.wkey[warp] = c;
+            // (a warp may already write column j + 1's key while a slower one
+            // still reads column j's: the keys alternate between two buffers)
+            if (lane == 0) sm.wkey[buf][warp] = c;
             __syncthreads();
-            Cand<T> cc = lane < NW ? sm.wkey[lane] : Cand<T>::none();
+            Cand<T> cc = lane < NW ? sm.wkey[buf][lane] : Cand<T>::none();
             cc = warp_best(cc);
             const int ci = cc.idx();
             const bool holds_diag = j >= rbase && j < rbase + rpc;
