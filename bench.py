@@ -540,6 +540,47 @@ def config_report(torch, solver, inputs, Ad, Bd, Xtrue, n, fp64_ms):
     return rows
 
 
+def run_fig4(args):
+    """The paper's Fig. 4 experiment (Section 4) on the batched solver: for
+    each condition number kappa (half-decade steps from 10^0.5 to 10^10) and
+    each factor precision p in {fp32, fp16, bf16}, 200 random 200 x 200
+    systems of prescribed kappa are solved in one mp_gesv_batched launch
+    with classical refinement, at most 30 corrections and no FP64 fallback.
+    Per (p, kappa): the mean number of corrections until the FP64 floor (a
+    system that does not converge counts as 30, the paper's convention),
+    the fraction that converged, and the prediction
+    ceil(ln u64 / (ln u_p + ln kappa)) where kappa u_p < 1.  One JSON line."""
+    import torch
+    from paper_0808_2794_gb300 import inputs, solver
+    torch.cuda.set_device(0)
+    kappas = [10.0 ** (0.5 * k) for k in range(1, 21)]
+    uu = {"fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+    u64 = 2.0 ** -53
+    rows = []
+    t0 = time.perf_counter()
+    for kappa, As, Bs, Xs in inputs.conditioned_batch_family(200, args.fig4_count, kappas, seed=0):
+        dA = [torch.from_numpy(a).cuda() for a in As]
+        dB = [torch.from_numpy(b).cuda() for b in Bs]
+        for prec in ("fp32", "fp16", "bf16"):
+            plan = solver.BatchedPlan(dA, dB, prec=prec, itermax=30, allow_fallback=False)
+            plan.run()
+            torch.cuda.synchronize()
+            it = plan.iter.astype(np.int64)
+            conv = (plan.flags & (solver.FLAG_NOT_CONVERGED | solver.FLAG_STALLED |
+                                  solver.FLAG_LOWP_BREAKDOWN)) == 0
+            counted = np.where(conv, it, 30)
+            ks = kappa * uu[prec]
+            pred = int(np.ceil(np.log(u64) / (np.log(uu[prec]) + np.log(kappa)))) if ks < 1 else None
+            rows.append({"prec": prec, "kappa": kappa, "kappa_u": ks, "mean_iter": float(counted.mean()),
+                         "mean_iter_converged": float(it[conv].mean()) if conv.any() else None,
+                         "frac_converged": float(conv.mean()), "prediction": pred})
+    line = {"metric": "Fig. 4: mean corrections to the FP64 floor vs condition number (200x200)",
+            "workload": f"{args.fig4_count} random 200x200 systems per kappa, A = U diag(s) V^T, Haar U, V",
+            "itermax": 30, "fallback": False, "seconds": time.perf_counter() - t0, "table": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,7 +591,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--prec", default="fp16x3")
     ap.add_argument("--refine", default="classical", choices=["classical", "gmres", "auto"])
-    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint"],
+    ap.add_argument("--fig4-count", type=int, default=200)
+    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint", "fig4"],
                     help="lu: the headline dense solve; the others time the secondary "
                          "workloads (SPD Cholesky, batched small systems, adjoint solve)")
     ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
@@ -564,6 +606,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "fig4":
+        return run_fig4(args)
     if args.workload != "lu":
         return run_secondary(args)
 

@@ -83,6 +83,32 @@ def conditioned_family(n: int, kappas, nrhs: int = 1, spd: bool = False, seed: i
         yield kappa, A, np.asfortranarray(A @ X), X
 
 
+def conditioned_batch_family(n: int, count: int, kappas, seed: int = 0):
+    """The Fig. 4 protocol (Section 4): for every kappa in kappas, `count`
+    random n x n general systems of 2-norm condition number kappa,
+    A_i = U_i diag(s) V_i^T with Haar U_i, V_i and s_j = kappa^{-j/(n-1)},
+    X_true ~ U[-1,1], b = A x_true (nrhs = 1).  The pairs (U_i, V_i) and
+    x_true,i are drawn once (in the order U_1, V_1, x_1, U_2, ...) and reused
+    for every kappa.  Yields (kappa, As, Bs, Xs) with lists of length count."""
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for _ in range(count):
+        U = haar_orthogonal(rng, n)
+        V = haar_orthogonal(rng, n)
+        x = rng.uniform(-1.0, 1.0, size=(n, 1))
+        pairs.append((U, V, np.asfortranarray(x)))
+    i = np.arange(n, dtype=np.float64)
+    for kappa in kappas:
+        s = kappa ** (-i / max(n - 1, 1))
+        As, Bs, Xs = [], [], []
+        for U, V, x in pairs:
+            A = np.asfortranarray((U * s[None, :]) @ V.T)
+            As.append(A)
+            Bs.append(np.asfortranarray(A @ x))
+            Xs.append(x)
+        yield kappa, As, Bs, Xs
+
+
 def batched_systems(count: int = 4096, seed: int = 0, nmin: int = 16, nmax: int = 512,
                     max_nrhs: int = 4):
     """``count`` independent systems, n = round(exp(U[ln nmin, ln nmax])),
