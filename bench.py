@@ -239,7 +239,12 @@ def run_secondary(args):
     import ctypes
     import torch
     from paper_0808_2794_gb300 import inputs, solver
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1 and args.workload == "batched":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     lib = solver.load()
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -256,10 +261,13 @@ def run_secondary(args):
         cfg = {"workload": f"SPD Cholesky solve, A = U diag(s) U^T, kappa={args.kappa:g}, n={n}, nrhs={nrhs}"}
     elif args.workload == "batched":
         As, Bs, _ = inputs.batched_systems(count=4096, seed=0)
-        dA = [torch.from_numpy(a).cuda() for a in As]
-        dB = [torch.from_numpy(b).cuda() for b in Bs]
+        # several ranks: the batch is spread by cost n^3, longest first
+        # (solver.shard_by_cost); each rank solves its share, no exchange
+        mine = solver.shard_by_cost([a.shape[0] for a in As], ws)[rank] if dist else list(range(len(As)))
+        dA = [torch.from_numpy(As[i]).cuda() for i in mine]
+        dB = [torch.from_numpy(Bs[i]).cuda() for i in mine]
         prec = args.prec if args.prec in ("fp32", "bf16", "fp16") else "fp32"
-        flops = sum(2.0 * a.shape[0] ** 3 / 3.0 for a in As)
+        flops = sum(2.0 * a.shape[0] ** 3 / 3.0 for a in As)  # the whole batch (strong scaling)
         plan = solver.BatchedPlan(dA, dB, prec=prec)  # argument tables built once, outside the timing
 
         def step():
@@ -287,6 +295,8 @@ def run_secondary(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     launches0 = solver.launch_count()
     ev[0].record(stream)
     out = None
@@ -294,12 +304,24 @@ def run_secondary(args):
         out = step()
     ev[1].record(stream)
     torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]) / args.steps, dist, "cuda")
     value = flops / (ms * 1e-3) / 1e9
+    if dist:
+        got = [None] * ws
+        dist.all_gather_object(got, out)
+        out = {"iter_max": max(g["iter_max"] for g in got), "flags_or": int(np.bitwise_or.reduce([g["flags_or"] for g in got])),
+               "n_fallback": sum(g["n_fallback"] for g in got)}
+        extra["scaling"] = "strong"
+        extra["parallelism"] = f"batch sharded by n^3 over {ws} ranks"
+        dist.destroy_process_group()
+        if rank != 0:
+            return 0
     line = {"metric": metric, "value": value, "unit": "GFLOP/s" if args.workload != "adjoint" else "GB/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "n_gpus": ws if dist else 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "dtype": f"{args.prec}-factor/f64-refine", "data": "synthetic",
-            "config": cfg, "gpu_launches": solver.launch_count() - launches0,
+            "config": cfg, "gpu_launches": solver.launch_count() - launches0, **extra,
             "solve": {k: v for k, v in (out or {}).items() if not isinstance(v, list)}}
     print(json.dumps(line), flush=True)
     return 0

@@ -298,6 +298,24 @@ MP_API int mp_residual(int n, int nrhs, const double *dA, int lda, const double 
                 const double *dB, int ldb, double *dR, int ldr, void *work,
                 size_t work_bytes, void *stream);
 
+/* Self-test of failure detection (no counterpart in the paper).  Every
+ * device-side wait of the library is bounded: after about one second it gives
+ * up, sets MP_FLAG_TIMEOUT and the kernel returns, so the host sees an error
+ * status instead of a hung GPU.  This call runs one of those waits on a
+ * condition that nothing satisfies, with the caller's limit, and reports what
+ * the kernel recorded.  site: 2 = the grid barrier of the triangular solves
+ * (a generation that needs one arrival more than the grid has), 3 = the
+ * panel kernel's mbarrier wait, 4 = the tensor-core kernels' mbarrier wait
+ * (both expecting 16 bytes that nothing sends).  limit_ns in [1, 1e9].  work:
+ * DEVICE scratch of mp_selftest_workspace_bytes() bytes.  On return *flags
+ * (host) holds the recorded MP_FLAG_* bits, *site_out the recorded site and
+ * *passed (site 2) the CTAs that got past the barrier (0 when the timeout
+ * path works); any of them may be NULL.  Returns 0 once the kernel has
+ * returned, -i for an illegal argument i, or a CUDA error (<= -1000). */
+MP_API size_t mp_selftest_workspace_bytes(void);
+MP_API int mp_selftest_wait_timeout(int site, unsigned long long limit_ns, void *work, size_t work_bytes,
+                                    unsigned *flags, int *site_out, int *passed, void *stream);
+
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  * ------------------------------------------------------------------------ */

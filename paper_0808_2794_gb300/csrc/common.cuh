@@ -95,26 +95,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded spin on a device flag written by another CTA of the same launch.
-// Gives up after about one second (and after a fixed number of polls, in
-// case the timer does not advance), records the site and returns false.
-__device__ __forceinline__ bool wait_flag_geq(const volatile int *flag, int target,
-                                              MpDevStatus *st, int site) {
-    if (*flag >= target) { __threadfence(); return true; }
-    const unsigned long long t0 = global_ns();
-    long long polls = 0;
-    while (*flag < target) {
-        if (++polls > (1LL << 24) || global_ns() - t0 > 1000000000ULL) {
-            mp_flag(st, MP_FLAG_TIMEOUT);
-            atomicExch(&st->timeout_site, site);
-            return false;
-        }
-        __nanosleep(64);
-    }
-    __threadfence();
-    return true;
-}
-
 // Counts kernel launches (every launch wrapper calls it).
 void mp_note_launch(int k = 1);
 

@@ -204,3 +204,14 @@ cudaError_t launch_correct(int n, int k, const double *Z, long ldz, const double
                            cudaStream_t s);
 // dst = src / d
 cudaError_t launch_scale(int n, const double *src, double d, double *dst, cudaStream_t s);
+
+// ---- timeout paths of the bounded waits (self-test) --------------------------
+// Each runs one of the library's bounded waits on a condition nothing
+// satisfies, with the given limit, recording MP_FLAG_TIMEOUT and the site in st.
+// bar: two zeroed words; passed: CTAs that got past the grid barrier;
+// abort_flag: a zeroed word.
+cudaError_t launch_selftest_grid_barrier(unsigned *bar, MpDevStatus *st, unsigned long long limit_ns, int *passed,
+                                         cudaStream_t s);
+cudaError_t launch_selftest_panel_mbar(MpDevStatus *st, unsigned long long limit_ns, cudaStream_t s);
+cudaError_t launch_selftest_tc_mbar(MpDevStatus *st, const int *abort_flag, unsigned long long limit_ns,
+                                    cudaStream_t s);

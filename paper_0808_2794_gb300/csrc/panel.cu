@@ -129,14 +129,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait (about one second); false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+// Bounded wait (about one second, or limit_ns); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity,
+                                                  unsigned long long limit_ns = 1000000000ULL) {
     for (int i = 0; i < 64; ++i)  // the usual case: the data arrives within a few polls
         if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long long i = 1;; ++i) {
         if (mbar_try(a, parity)) return true;
-        if ((i & 255) == 0 && (global_ns() - t0 > 1000000000ULL || i > (1LL << 30))) return false;
+        if ((i & 255) == 0 && (global_ns() - t0 > limit_ns || i > (1LL << 30))) return false;
     }
 }
 // 16 bytes to the shared memory of another CTA of the cluster, counted on its mbarrier.
@@ -660,7 +661,29 @@ cudaError_t launch_panel_t(T *P, long ld, int m, int ncols, int row0, int32_t *i
     return cudaLaunchKernelEx(&cfg, kern, P, ld, m, ncols, row0, ipiv, moves, nmoves, st, linv, prev);
 }
 
+// Timeout path of the panel's bounded mbarrier wait, for the self-test: the
+// barrier expects 16 bytes that nothing sends (site 3).
+__global__ void selftest_mbar_kernel(MpDevStatus *st, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init_(smem_u32(&bar), 1);
+        mbar_arm(smem_u32(&bar), 16);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(smem_u32(&bar), 0u, limit_ns);
+    if (!ok && threadIdx.x == 0) {
+        mp_flag(st, MP_FLAG_TIMEOUT);
+        atomicExch(&st->timeout_site, 3);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_panel_mbar(MpDevStatus *st, unsigned long long limit_ns, cudaStream_t s) {
+    mp_note_launch();
+    selftest_mbar_kernel<<<1, 32, 0, s>>>(st, limit_ns);
+    return cudaGetLastError();
+}
 
 // Base panel width for a panel of height m.  One CTA keeps 1024 rows (512
 // threads x 2 rows) of the active columns in registers and the finished part

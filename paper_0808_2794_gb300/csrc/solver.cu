@@ -1653,3 +1653,36 @@ extern "C" int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *d
     }
     return 0;
 }
+
+// ---------------------------------------------------------------------------
+// self-test of the bounded waits' timeout path
+// ---------------------------------------------------------------------------
+extern "C" size_t mp_selftest_workspace_bytes(void) { return 256; }
+
+extern "C" int mp_selftest_wait_timeout(int site, unsigned long long limit_ns, void *work, size_t work_bytes,
+                                        unsigned *flags, int *site_out, int *passed, void *stream) {
+    g_err[0] = 0;
+    if (site < 2 || site > 4) return mp_arg_fail(1, "site must be 2 (grid barrier), 3 or 4 (mbarrier waits)");
+    if (limit_ns < 1 || limit_ns > 1000000000ULL) return mp_arg_fail(2, "limit_ns must be in [1, 1e9]");
+    if (!work) return mp_arg_fail(3, "workspace is NULL");
+    if (work_bytes < mp_selftest_workspace_bytes()) return mp_arg_fail(4, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(work);
+    MpDevStatus *st = reinterpret_cast<MpDevStatus *>(w);
+    unsigned *bar = reinterpret_cast<unsigned *>(w + 64);
+    int *dpassed = reinterpret_cast<int *>(w + 128);
+    int *abort_flag = reinterpret_cast<int *>(w + 192);
+    MP_CUDA_TRY(cudaMemsetAsync(work, 0, mp_selftest_workspace_bytes(), s));
+    if (site == 2) MP_CUDA_TRY(launch_selftest_grid_barrier(bar, st, limit_ns, dpassed, s));
+    else if (site == 3) MP_CUDA_TRY(launch_selftest_panel_mbar(st, limit_ns, s));
+    else MP_CUDA_TRY(launch_selftest_tc_mbar(st, abort_flag, limit_ns, s));
+    MpDevStatus h;
+    int hp = 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaMemcpyAsync(&hp, dpassed, sizeof hp, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags) *flags = h.flags;
+    if (site_out) *site_out = h.timeout_site;
+    if (passed) *passed = hp;
+    return 0;
+}

@@ -85,15 +85,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false after about one second.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int *abort_flag) {
+// Bounded wait: false after about one second (or limit_ns).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int *abort_flag,
+                                          unsigned long long limit_ns = 1000000000ULL) {
     if (mbar_try_wait(a, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long long i = 1;; ++i) {
         if (mbar_try_wait(a, parity)) return true;
         if ((i & 255) == 0) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > 1000000000ULL || i > (1LL << 32)) return false;
+            if (global_ns() - t0 > limit_ns || i > (1LL << 32)) return false;
         }
     }
 }
@@ -570,7 +571,30 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     return cudaGetLastError();
 }
 
+// Timeout path of the tensor-core kernels' bounded mbarrier wait, for the
+// self-test: the barrier expects 16 bytes that nothing sends (site 4).
+__global__ void selftest_tc_mbar_kernel(MpDevStatus *st, const int *abort_flag, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(16u) : "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(smem_u32(&bar), 0u, abort_flag, limit_ns);
+    if (!ok && threadIdx.x == 0) {
+        mp_flag(st, MP_FLAG_TIMEOUT);
+        atomicExch(&st->timeout_site, 4);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_tc_mbar(MpDevStatus *st, const int *abort_flag, unsigned long long limit_ns,
+                                    cudaStream_t s) {
+    mp_note_launch();
+    selftest_tc_mbar_kernel<<<1, 32, 0, s>>>(st, abort_flag, limit_ns);
+    return cudaGetLastError();
+}
 
 size_t tc_workspace_bytes(int n, int nb, int prec) {
     if (prec != MP_PREC_BF16 && prec != MP_PREC_FP16 && prec != MP_PREC_FP16X3 && prec != MP_PREC_E4M3) return 0;

@@ -74,15 +74,19 @@ base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restr
         if (c < bs) Uinv[dst + (long)i * BI + c] = x[i][c];
 }
 
-// ---- grid-wide barrier for a cooperative launch (bounded wait)
+// ---- grid-wide barrier for a cooperative launch (bounded wait: after
+//      limit_ns without the last arrival a CTA records a timeout and returns
+//      false; `expected` arrivals complete a generation, normally the grid)
 __device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, MpDevStatus *st,
-                                             bool *abort_s) {
+                                             bool *abort_s, unsigned long long limit_ns = 1000000000ULL,
+                                             unsigned expected = 0) {
+    if (expected == 0) expected = gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == expected - 1) {
             *count = 0;
             __threadfence();
             atomicAdd((unsigned *)gen, 1u);
@@ -90,7 +94,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned 
             const unsigned long long t0 = global_ns();
             long long polls = 0;
             while (*gen == g) {
-                if (++polls > (1LL << 24) || global_ns() - t0 > 1000000000ULL) {
+                if (++polls > (1LL << 24) || global_ns() - t0 > limit_ns) {
                     mp_flag(st, MP_FLAG_TIMEOUT);
                     atomicExch(&st->timeout_site, 2);
                     *abort_s = true;
@@ -270,7 +274,27 @@ cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, con
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
+// Timeout path of the grid barrier, for the self-test: every CTA arrives,
+// but a generation needs one arrival more than the grid has, so no CTA can
+// pass; each gives up after limit_ns and records the timeout (site 2).
+__global__ void selftest_grid_barrier_kernel(unsigned *count, unsigned *gen, MpDevStatus *st,
+                                             unsigned long long limit_ns, int *passed) {
+    __shared__ bool abort_s;
+    if (threadIdx.x == 0) abort_s = false;
+    __syncthreads();
+    if (grid_barrier(count, gen, st, &abort_s, limit_ns, gridDim.x + 1) && threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_grid_barrier(unsigned *bar, MpDevStatus *st, unsigned long long limit_ns, int *passed,
+                                         cudaStream_t s) {
+    unsigned *count = bar, *gen = bar + 1;
+    void *args[] = {&count, &gen, &st, &limit_ns, &passed};
+    mp_note_launch();
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(selftest_grid_barrier_kernel), dim3(2), dim3(32),
+                                       args, 0, s);
+}
 
 template <typename T>
 int trsv_inverse_block(int n) {

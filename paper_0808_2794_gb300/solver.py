@@ -90,6 +90,9 @@ _SIGS = {
     "mp_noalloc_scratch_bytes": (_Z, []),
     "mp_gesv_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(mp_opts),
                              ctypes.POINTER(mp_stats), _P]),
+    "mp_selftest_workspace_bytes": (_Z, []),
+    "mp_selftest_wait_timeout": (_I, [_I, ctypes.c_ulonglong, _P, _Z, ctypes.POINTER(ctypes.c_uint),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
     "mp_profile_enable": (None, [ctypes.c_uint]),
     "mp_profile_collect": (_I, [_P, _P, _P]),
     "mp_launch_count": (ctypes.c_longlong, []),
@@ -525,3 +528,69 @@ def lowp_gemm_update(C, L, U, prec="bf16", work=None, stream=None):
                                    C.data_ptr(), C.stride(0), work.data_ptr(), work.numel(),
                                    _stream_ptr(stream)), "mp_lowp_gemm_update")
     return C
+
+
+def selftest_wait_timeout(site: int, limit_ns: int, stream=None):
+    """Runs one of the library's bounded device waits on a condition nothing
+    satisfies (site 2: triangular-solve grid barrier, 3: panel mbarrier wait,
+    4: tensor-core mbarrier wait) with the given limit.  Returns (flags,
+    recorded site, CTAs past the barrier)."""
+    lib = load()
+    work = workspace(lib.mp_selftest_workspace_bytes())
+    fl, si, pa = ctypes.c_uint(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.mp_selftest_wait_timeout(int(site), int(limit_ns), work.data_ptr(), work.numel(), ctypes.byref(fl),
+                                        ctypes.byref(si), ctypes.byref(pa), _stream_ptr(stream)),
+           "mp_selftest_wait_timeout")
+    return fl.value, si.value, pa.value
+
+
+def shard_by_cost(ns, world: int):
+    """Partition of a batch of systems over `world` ranks by cost n^3 (the
+    O(n^3) factorization dominates): systems in decreasing n^3 (ties: lower
+    index first) each go to the rank with the least cost so far (ties: lower
+    rank).  Returns one list of system indices per rank, in the order the
+    systems were assigned (longest first)."""
+    order = sorted(range(len(ns)), key=lambda i: (-int(ns[i]) ** 3, i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += int(ns[i]) ** 3
+    return parts
+
+
+def gesv_batched_sharded(ns, get_system, group=None, solve=None, **kw):
+    """A batch of independent systems spread over the ranks of a
+    torch.distributed group by cost (shard_by_cost), each rank solving its
+    share in one mp_gesv_batched launch; there is no exchange on the data
+    path.  ns: every system's order (the same list on every rank);
+    get_system(i) -> (A_i, B_i) device tensors of system i, called only for
+    this rank's systems; solve(As, Bs) -> (Xs, iter, flags) defaults to
+    gesv_batched with **kw.  Afterwards one all-gather gives every rank the
+    iteration counts and flags of the whole batch.  Returns (mine, Xs, iter,
+    flags): this rank's system indices and solutions, and the batch's
+    iter/flags as numpy arrays indexed by system."""
+    import numpy as np
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    mine = shard_by_cost(ns, world)[rank]
+    if solve is None:
+        def solve(As, Bs):
+            Xs, _, it, fl, _ = gesv_batched(As, Bs, **kw)
+            return Xs, it, fl
+    if mine:
+        systems = [get_system(i) for i in mine]
+        Xs, it, fl = solve([a for a, _ in systems], [b for _, b in systems])
+    else:
+        Xs, it, fl = [], np.zeros(0, dtype=np.int32), np.zeros(0, dtype=np.uint32)
+    local = (list(mine), [int(v) for v in it], [int(v) for v in fl])
+    gathered = [None] * world
+    dist.all_gather_object(gathered, local, group=group)
+    iters = np.full(len(ns), np.iinfo(np.int32).min, dtype=np.int64)
+    flags = np.zeros(len(ns), dtype=np.uint64)
+    for idx, its, fls in gathered:
+        iters[idx] = its
+        flags[idx] = fls
+    return mine, Xs, iters, flags
