@@ -39,6 +39,13 @@ constexpr int NT = 256;
 constexpr int kMaxN = MP_BATCH_MAX_N;
 constexpr int kMaxRhs = 8;
 
+// 16-byte vector of T and its width
+template <typename T> struct V16Of;
+template <> struct V16Of<float> { using type = float4; };
+template <> struct V16Of<double> { using type = double2; };
+template <typename T> using V16 = typename V16Of<T>::type;
+template <typename T> constexpr int VW16 = 16 / (int)sizeof(T);
+
 template <typename T> struct BCfg;
 template <> struct BCfg<float> { static constexpr int NB = 32; };
 template <> struct BCfg<double> { static constexpr int NB = 16; };
@@ -335,7 +342,17 @@ __device__ void lu_solve(int n, int nrhs, const T *W, int ldw, const T *Dinv, T 
             if (c < nrhs && r < bs) {
                 const T *drow = D + r * 32;
                 T s = T(0);
-                for (int k = 0; k < bs; ++k) s = fma(drow[k], v[c * kMaxN + r0 + k], s);
+                if (bs == 32) {  // whole 16-byte pieces of the row, same order
+#pragma unroll
+                    for (int q = 0; q < 32 / VW16<T>; ++q) {
+                        const V16<T> dv = reinterpret_cast<const V16<T> *>(drow)[q];
+                        const T *pd = reinterpret_cast<const T *>(&dv);
+#pragma unroll
+                        for (int e = 0; e < VW16<T>; ++e) s = fma(pd[e], v[c * kMaxN + r0 + q * VW16<T> + e], s);
+                    }
+                } else {
+                    for (int k = 0; k < bs; ++k) s = fma(drow[k], v[c * kMaxN + r0 + k], s);
+                }
                 tmp[c * 32 + r] = s;
             }
             __syncthreads();
@@ -346,11 +363,77 @@ __device__ void lu_solve(int n, int nrhs, const T *W, int ldw, const T *Dinv, T 
                 const int cc = e / (hi - lo), i = lo + e % (hi - lo);
                 const T *wr = W + (long)i * ldw + r0;
                 T s = v[cc * kMaxN + i];
-                for (int j = 0; j < bs; ++j) s = fma(-wr[j], v[cc * kMaxN + r0 + j], s);
+                if (bs == 32) {  // the row segment in 16-byte pieces (ldw and r0 are multiples of 4)
+#pragma unroll
+                    for (int q = 0; q < 32 / VW16<T>; ++q) {
+                        const V16<T> wv = reinterpret_cast<const V16<T> *>(wr)[q];
+                        const T *pw = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+                        for (int e = 0; e < VW16<T>; ++e) s = fma(-pw[e], v[cc * kMaxN + r0 + q * VW16<T> + e], s);
+                    }
+                } else {
+                    for (int j = 0; j < bs; ++j) s = fma(-wr[j], v[cc * kMaxN + r0 + j], s);
+                }
                 v[cc * kMaxN + i] = s;
             }
             __syncthreads();
         }
+    }
+}
+
+// r = b - A x (FP64) for the thread's rows i = tid and tid + NT (n <= 2 NT),
+// products in column order per row, 16 columns per batch with both rows'
+// loads in flight; rloc[c], xloc[c] receive the thread's max |r_c| and |x_c|.
+// NR >= nrhs bounds the unrolled right-hand-side loops.
+template <int NR>
+__device__ __forceinline__ void residual_rows(const BatchSys &d, int n, int nrhs, const double *xs, double *rloc,
+                                              double *xloc) {
+    const int i0 = threadIdx.x, i1 = threadIdx.x + NT;
+    const bool v0 = i0 < n, v1 = i1 < n;
+    double acc0[NR], acc1[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) { acc0[c] = 0.0; acc1[c] = 0.0; }
+    const double *a0p = d.A + i0, *a1p = d.A + i1;
+    int j = 0;
+    for (; j + 16 <= n; j += 16) {
+        double a0[16], a1[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            a0[t] = v0 ? a0p[(long)(j + t) * d.lda] : 0.0;
+            a1[t] = v1 ? a1p[(long)(j + t) * d.lda] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if (c < nrhs) {
+                    const double x = xs[c * kMaxN + j + t];
+                    acc0[c] = fma(a0[t], x, acc0[c]);
+                    acc1[c] = fma(a1[t], x, acc1[c]);
+                }
+    }
+    for (; j < n; ++j) {
+        const double a0 = v0 ? a0p[(long)j * d.lda] : 0.0, a1 = v1 ? a1p[(long)j * d.lda] : 0.0;
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            if (c < nrhs) {
+                const double x = xs[c * kMaxN + j];
+                acc0[c] = fma(a0, x, acc0[c]);
+                acc1[c] = fma(a1, x, acc1[c]);
+            }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = h ? i1 : i0;
+        if (i >= n) continue;
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            if (c < nrhs) {
+                const double r = d.B[(long)c * d.ldb + i] - (h ? acc1[c] : acc0[c]);
+                d.R[(long)c * n + i] = r;
+                rloc[c] = fmax(rloc[c], (r == r) ? fabs(r) : INFINITY);
+                xloc[c] = fmax(xloc[c], fabs(xs[c * kMaxN + i]));
+            }
     }
 }
 
@@ -381,30 +464,29 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
         for (int i = tid; i < n; i += NT) d.perm[i] = i;
         __syncthreads();
         // ---- convert: row sums of |A| (fixed order per row), W = fl(A) through the panel buffer
-        double rmax = 0.0;
-        bool bad = false;
-        for (int i = tid; i < n; i += NT) {
-            // 16 loads in flight per thread, summed in column order
-            double s = 0.0;
-            const double *ai = d.A + i;
-            int j = 0;
-            for (; j + 16 <= n; j += 16) {
-                double a[16];
-#pragma unroll
-                for (int t = 0; t < 16; ++t) a[t] = __ldcs(ai + (long)(j + t) * d.lda);
-#pragma unroll
-                for (int t = 0; t < 16; ++t) s += fabs(a[t]);
-            }
-            for (; j < n; ++j) s += fabs(ai[(long)j * d.lda]);
-            if (!(s <= 1.79769313486231570815e308)) bad = true;
-            rmax = fmax(rmax, s);
-        }
-        const double an = block_max(bad ? __longlong_as_double(0x7ff0000000000000LL) : rmax, sh);
+        // A is read once: column chunks of NB through the panel buffer, rows
+        // fixed per thread (tid, tid + NT) with the chunk's loads in flight,
+        // and the row sums of |A| taken from the same values in column order
+        double rsum[2] = {0.0, 0.0};
         for (int c0 = 0; c0 < n; c0 += NB) {
             const int w = min(NB, n - c0);
-            for (int e = tid; e < n * w; e += NT) {
-                const int i = e % n, j = e / n;
-                P[i * (NB + 1) + j] = (T)d.A[(long)(c0 + j) * d.lda + i];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = tid + h * NT;
+                if (i < n) {
+                    const double *ai = d.A + (long)c0 * d.lda + i;
+                    double a[NB];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) a[j] = j < w ? __ldcs(ai + (long)j * d.lda) : 0.0;
+                    double sacc = rsum[h];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j < w) {
+                            sacc += fabs(a[j]);
+                            P[i * (NB + 1) + j] = (T)a[j];
+                        }
+                    rsum[h] = sacc;
+                }
             }
             __syncthreads();
             for (int e = tid; e < n * w; e += NT) {
@@ -413,6 +495,15 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
             }
             __syncthreads();
         }
+        bool bad = false;
+        double rmax = 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (tid + h * NT < n) {
+                if (!(rsum[h] <= 1.79769313486231570815e308)) bad = true;
+                rmax = fmax(rmax, rsum[h]);
+            }
+        const double an = block_max(bad ? __longlong_as_double(0x7ff0000000000000LL) : rmax, sh);
         for (int c = 0; c < nrhs; ++c) {
             double m = 0.0;
             for (int i = tid; i < n; i += NT) m = fmax(m, fabs(d.B[(long)c * d.ldb + i]));
@@ -471,37 +562,10 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
             double rloc[kMaxRhs], xloc[kMaxRhs];
 #pragma unroll
             for (int c = 0; c < kMaxRhs; ++c) { rloc[c] = 0.0; xloc[c] = 0.0; }
-            for (int i = tid; i < n; i += NT) {
-                double acc[kMaxRhs];
-#pragma unroll
-                for (int c = 0; c < kMaxRhs; ++c) acc[c] = 0.0;
-                const double *ai = d.A + i;
-                int j = 0;
-                for (; j + 16 <= n; j += 16) {  // 16 loads in flight, products in column order
-                    double a[16];
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) a[t] = ai[(long)(j + t) * d.lda];
-#pragma unroll
-                    for (int t = 0; t < 16; ++t)
-#pragma unroll
-                        for (int c = 0; c < kMaxRhs; ++c)
-                            if (c < nrhs) acc[c] = fma(a[t], xs[c * kMaxN + j + t], acc[c]);
-                }
-                for (; j < n; ++j) {
-                    const double a = ai[(long)j * d.lda];
-#pragma unroll
-                    for (int c = 0; c < kMaxRhs; ++c)
-                        if (c < nrhs) acc[c] = fma(a, xs[c * kMaxN + j], acc[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < kMaxRhs; ++c)
-                    if (c < nrhs) {
-                        const double r = d.B[(long)c * d.ldb + i] - acc[c];
-                        d.R[(long)c * n + i] = r;
-                        rloc[c] = fmax(rloc[c], (r == r) ? fabs(r) : INFINITY);
-                        xloc[c] = fmax(xloc[c], fabs(xs[c * kMaxN + i]));
-                    }
-            }
+            if (nrhs <= 1) residual_rows<1>(d, n, nrhs, xs, rloc, xloc);
+            else if (nrhs <= 2) residual_rows<2>(d, n, nrhs, xs, rloc, xloc);
+            else if (nrhs <= 4) residual_rows<4>(d, n, nrhs, xs, rloc, xloc);
+            else residual_rows<8>(d, n, nrhs, xs, rloc, xloc);
             for (int c = 0; c < nrhs; ++c) {
                 const double rm = block_max(rloc[c], sh);
                 const double xm = block_max(xloc[c], sh);
