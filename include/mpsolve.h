@@ -180,6 +180,20 @@ MP_API int mp_gesv_batched(int batch, const int *n, const int *nrhs, const doubl
                            int32_t *const *ipiv, int *iter, unsigned *flags, int *info, void *work,
                            size_t work_bytes, const mp_opts *opts, void *stream);
 
+/* Tile schedule of the batched solver (no counterpart in the paper): the
+ * panel width (8, 16 or 32 columns) of each system's low-precision
+ * factorization by range of n.  Range i covers nmax[i-1] < n <= nmax[i]
+ * (nmax increasing, the last >= MP_BATCH_MAX_N).  The library starts from
+ * a table chosen on GB300 by the project's autotuner, which times every
+ * width on each range of n and writes the table into the library's sources;
+ * mp_batched_set_schedule replaces it for the process (count = 0 restores
+ * the built-in table) and is what the autotuner uses to time candidates.
+ * The schedule is process-wide: change it only while no batched solve is in
+ * flight.  Returns 0 or -i for an illegal argument i.  mp_batched_get_schedule
+ * copies up to cap entries and sets *count to the number of ranges. */
+MP_API int mp_batched_set_schedule(int count, const int *nmax, const int *nb);
+MP_API int mp_batched_get_schedule(int cap, int *count, int *nmax, int *nb);
+
 /* Adjoint of the solve (reverse-mode derivative of X = A^{-1} B; the paper
  * has no counterpart).  Given the FP64 cotangent G = dL/dX (n x nrhs),
  * computes Bbar = A^{-T} G (n x nrhs) and Abar = -Bbar X^T (n x n, FP64,

@@ -24,6 +24,7 @@
 // A system whose low-precision refinement fails is marked and re-solved by
 // the same kernel instantiated for FP64 (Section 4's fallback).
 #include "batched.cuh"
+#include "batched_schedule.h"
 #include "common.cuh"
 
 #include <cuda_bf16.h>
@@ -31,6 +32,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -523,7 +525,13 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
             continue;
         }
         // ---- factor
-        lu_factor<T, NB>(d, W, ldw, P, Us, sh, prec);
+        if constexpr (sizeof(T) == 4) {  // the panel width the schedule gave this system
+            if (d.nb == 8) lu_factor<T, 8>(d, W, ldw, P, Us, sh, prec);
+            else if (d.nb == 16) lu_factor<T, 16>(d, W, ldw, P, Us, sh, prec);
+            else lu_factor<T, 32>(d, W, ldw, P, Us, sh, prec);
+        } else {
+            lu_factor<T, NB>(d, W, ldw, P, Us, sh, prec);
+        }
         if (sh.flags & MP_FLAG_LOWP_BREAKDOWN) {
             if (tid == 0) { d.flags = sh.flags; d.iter = 0; d.info = sh.info; d.bwd = INFINITY; }
             __syncthreads();
@@ -675,6 +683,50 @@ size_t batched_layout(int batch, const int *n, const int *nrhs, bool fp64, size_
     return (off + 255) / 256 * 256;
 }
 
+// The active schedule: the compiled-in table unless mp_batched_set_schedule
+// replaced it (process-wide).
+namespace {
+std::mutex g_sched_mu;
+std::vector<int> g_sched_nmax(kBatchedNmax, kBatchedNmax + kBatchedRanges);
+std::vector<int> g_sched_nb(kBatchedNb, kBatchedNb + kBatchedRanges);
+int schedule_nb(int n) {
+    std::lock_guard<std::mutex> g(g_sched_mu);
+    for (size_t i = 0; i < g_sched_nmax.size(); ++i)
+        if (n <= g_sched_nmax[i]) return g_sched_nb[i];
+    return 32;
+}
+}  // namespace
+
+extern "C" int mp_batched_set_schedule(int count, const int *nmax, const int *nb) {
+    if (count < 0 || count > 64) return mp_arg_fail(1, "count must be in [0, 64]");
+    std::lock_guard<std::mutex> g(g_sched_mu);
+    if (count == 0) {
+        g_sched_nmax.assign(kBatchedNmax, kBatchedNmax + kBatchedRanges);
+        g_sched_nb.assign(kBatchedNb, kBatchedNb + kBatchedRanges);
+        return 0;
+    }
+    if (!nmax) return mp_arg_fail(2, "nmax is NULL");
+    if (!nb) return mp_arg_fail(3, "nb is NULL");
+    for (int i = 0; i < count; ++i) {
+        if (nmax[i] < 1 || (i > 0 && nmax[i] <= nmax[i - 1])) return mp_arg_fail(2, "nmax must increase");
+        if (nb[i] != 8 && nb[i] != 16 && nb[i] != 32) return mp_arg_fail(3, "nb must be 8, 16 or 32");
+    }
+    if (nmax[count - 1] < MP_BATCH_MAX_N) return mp_arg_fail(2, "the last range must reach MP_BATCH_MAX_N");
+    g_sched_nmax.assign(nmax, nmax + count);
+    g_sched_nb.assign(nb, nb + count);
+    return 0;
+}
+
+extern "C" int mp_batched_get_schedule(int cap, int *count, int *nmax, int *nb) {
+    std::lock_guard<std::mutex> g(g_sched_mu);
+    if (count) *count = (int)g_sched_nmax.size();
+    for (int i = 0; i < (int)g_sched_nmax.size() && i < cap; ++i) {
+        if (nmax) nmax[i] = g_sched_nmax[i];
+        if (nb) nb[i] = g_sched_nb[i];
+    }
+    return 0;
+}
+
 int batched_run(int batch, const int *n, const int *nrhs, const double *const *A, const int *lda,
                 const double *const *B, const int *ldb, double *const *X, const int *ldx, int32_t *const *ipiv,
                 int *iter, unsigned *flags, int *info, void *work, const mp_opts &o, cudaStream_t s,
@@ -700,6 +752,7 @@ int batched_run(int batch, const int *n, const int *nrhs, const double *const *A
         d.ldb = ldb[b];
         d.ldx = ldx[b];
         d.ldw = (nn + 3) / 4 * 4;
+        d.nb = schedule_nb(nn);
         d.A = A[b];
         d.B = B[b];
         d.X = X[b];

@@ -16,7 +16,7 @@ struct BatchSys {
     void *Dinv;   // inverses of the 32 x 32 diagonal blocks of L and U
     int iter, info;
     unsigned flags;
-    int pad;
+    int nb;       // panel width of the low-precision factorization (from the schedule)
     double bwd;
 };
 

@@ -90,6 +90,8 @@ _SIGS = {
     "mp_noalloc_scratch_bytes": (_Z, []),
     "mp_gesv_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(mp_opts),
                              ctypes.POINTER(mp_stats), _P]),
+    "mp_batched_set_schedule": (_I, [_I, _P, _P]),
+    "mp_batched_get_schedule": (_I, [_I, ctypes.POINTER(ctypes.c_int), _P, _P]),
     "mp_selftest_workspace_bytes": (_Z, []),
     "mp_selftest_wait_timeout": (_I, [_I, ctypes.c_ulonglong, _P, _Z, ctypes.POINTER(ctypes.c_uint),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
@@ -594,3 +596,28 @@ def gesv_batched_sharded(ns, get_system, group=None, solve=None, **kw):
         iters[idx] = its
         flags[idx] = fls
     return mine, Xs, iters, flags
+
+
+def batched_schedule():
+    """The batched solver's active tile schedule: list of (nmax, panel width)."""
+    import numpy as np
+    lib = load()
+    cnt = ctypes.c_int(0)
+    nm = np.zeros(64, dtype=np.int32)
+    nb = np.zeros(64, dtype=np.int32)
+    _check(lib.mp_batched_get_schedule(64, ctypes.byref(cnt), nm.ctypes.data, nb.ctypes.data),
+           "mp_batched_get_schedule")
+    return [(int(nm[i]), int(nb[i])) for i in range(cnt.value)]
+
+
+def set_batched_schedule(entries=None):
+    """Replaces the batched solver's tile schedule for this process with
+    entries [(nmax, panel width), ...]; None restores the built-in table."""
+    import numpy as np
+    lib = load()
+    if not entries:
+        _check(lib.mp_batched_set_schedule(0, None, None), "mp_batched_set_schedule")
+        return
+    nm = np.array([e[0] for e in entries], dtype=np.int32)
+    nb = np.array([e[1] for e in entries], dtype=np.int32)
+    _check(lib.mp_batched_set_schedule(len(entries), nm.ctypes.data, nb.ctypes.data), "mp_batched_set_schedule")

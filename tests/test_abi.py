@@ -70,3 +70,22 @@ def test_workspace_queries_scale(lib):
     o.allow_fallback = 0
     assert lib.mp_gesv_workspace_bytes(2048, 1, ctypes.byref(o)) < w2 * 0.75
     assert lib.mp_factor_ld(1) == 32 and lib.mp_factor_ld(33) == 64
+
+
+def test_batched_schedule_set_get_and_validation():
+    """The batched solver's tile schedule (host-side state, no GPU needed):
+    replaced, read back, validated and restored."""
+    from paper_0808_2794_gb300 import solver
+    base = solver.batched_schedule()
+    assert base and base[-1][0] >= solver.BATCH_MAX_N
+    assert all(nb in (8, 16, 32) for _, nb in base)
+    try:
+        solver.set_batched_schedule([(64, 8), (512, 16)])
+        assert solver.batched_schedule() == [(64, 8), (512, 16)]
+        for bad in ([(64, 12), (512, 16)], [(128, 16), (64, 16)], [(256, 16)]):
+            with pytest.raises(solver.MpError):
+                solver.set_batched_schedule(bad)
+        assert solver.batched_schedule() == [(64, 8), (512, 16)]
+    finally:
+        solver.set_batched_schedule(None)
+    assert solver.batched_schedule() == base

@@ -130,3 +130,22 @@ def test_batched_config_size(torch, mp, orc, prec):
     assert np.all(fl == 0) and np.all(it >= 0)
     for A, B, X in zip(As, Bs, Xs):
         assert np.all(orc.bwd_err(A, host(X).reshape(B.shape), B) <= 1e-14)
+
+
+@pytest.mark.parametrize("nb", [8, 16, 32])
+def test_batched_every_panel_width(torch, mp, orc, nb):
+    """Every panel width the autotuner can choose gives correct solutions:
+    a batch of uneven systems solved with the schedule forced to one width."""
+    As, Bs, Xs = inputs.batched_systems(count=40, seed=5, nmin=16, nmax=200)
+    mp.set_batched_schedule([(mp.BATCH_MAX_N, nb)])
+    try:
+        Xo, piv, it, fl, info = mp.gesv_batched([torch.from_numpy(a).cuda() for a in As],
+                                                [torch.from_numpy(b).cuda() for b in Bs])
+    finally:
+        mp.set_batched_schedule(None)
+    assert np.all(fl == 0) and np.all(it >= 0), (it, fl)
+    for a, b, x, p in zip(As, Bs, Xo, piv):
+        xh = x.cpu().numpy().reshape(a.shape[0], -1)
+        assert np.all(orc.bwd_err(a, xh, b) <= 1e-14)
+        ph = p.cpu().numpy()
+        assert np.all((ph >= np.arange(1, a.shape[0] + 1)) & (ph <= a.shape[0]))
