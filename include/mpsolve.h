@@ -58,9 +58,11 @@ typedef enum {
                            accumulation: about FP32 accuracy at fp16 tensor-core speed */
     MP_PREC_BF16 = 2,   /* trailing-update operands rounded to bfloat16, FP32 accumulation */
     MP_PREC_FP16 = 3,   /* trailing-update operands rounded to binary16, FP32 accumulation */
-    MP_PREC_E4M3 = 4,   /* trailing-update operands scaled by a power of two per operand and
-                           rounded to FP8 E4M3 (round to nearest even, saturating at 448),
-                           FP32 accumulation (tcgen05 kind::f8f6f4) */
+    MP_PREC_E4M3 = 4,   /* trailing-update operands scaled by a power of two per 128 x 128 block
+                           (block max below 2^8) and rounded to FP8 E4M3 (round to nearest even,
+                           saturating at 448); each 128-wide K-block's product is formed on the
+                           tensor cores (tcgen05 kind::f8f6f4) with FP32 accumulation and unscaled
+                           by its two blocks' scales */
     MP_PREC_FP64 = 5    /* no low precision: the plain double-precision solve that the paper
                            measures its speedups against (Section 3, Table 3: DGETRF + DGETRS,
                            DPOTRF + DPOTRS), FP64 factors on the GPU, x_0 from them and the same
@@ -296,9 +298,10 @@ MP_API int mp_getrs_lowp(int n, int nrhs, const float *dW, int ldw, const int32_
  * ldc >= N; ldl, ldu, ldc multiples of 4).  prec: MP_PREC_FP32 (plain FP32
  * FMA on CUDA cores), MP_PREC_BF16 / MP_PREC_FP16 (operands rounded to
  * nearest even, FP32 accumulation on tcgen05 tensor cores), MP_PREC_FP16X3
- * (split operands, three tensor-core products), MP_PREC_E4M3 (each operand
- * scaled by a power of two, max |x| below 2^8, rounded to E4M3; the product
- * unscaled in the FP32 epilogue).  work must hold
+ * (split operands, three tensor-core products), MP_PREC_E4M3 (every 128 x 128
+ * block of each operand scaled by its own power of two, block max below 2^8,
+ * rounded to E4M3; each K-block's product unscaled by its two blocks' scales
+ * in the FP32 epilogue).  work must hold
  * mp_lowp_gemm_workspace_bytes(M, N, K, prec). */
 MP_API size_t mp_lowp_gemm_workspace_bytes(int M, int N, int K, int prec);
 MP_API int mp_lowp_gemm_update(int prec, int M, int N, int K, const float *dL, int ldl,

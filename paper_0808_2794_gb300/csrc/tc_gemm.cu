@@ -14,6 +14,10 @@
 // issuer (tcgen05.mma.cta_group::1.kind::f16, FP32 accumulators in TMEM,
 // two 256-column accumulators so the epilogue of tile t overlaps the MMAs of
 // tile t+1), warps 2..9 = epilogue (tcgen05.ld, C - acc, coalesced stores).
+// E4M3 (kind::f8f6f4): every 128 x 128 block of L21 and of U12 has its own
+// power-of-two scale (block max below 2^8); the kernel runs once per 128-wide
+// K-block and the epilogue unscales each tile by its row block's and column
+// block's scales of that K-block before subtracting it from C.
 // Every mbarrier wait is bounded (about one second) and reports
 // MP_FLAG_TIMEOUT instead of hanging.
 #include <cuda.h>
@@ -49,6 +53,16 @@ constexpr int MAX_STAGES = 4;
 template <int SPLIT> struct TcCfg {
     static constexpr int STAGE_BYTES = SPLIT * (A_BYTES + B_BYTES);
     static constexpr int STAGES = SPLIT == 1 ? 4 : 2;
+};
+
+// Per-block scales of the E4M3 rung: the kernel handles K-block k_first
+// (launched once per K-block), and tile (ib, jb) is unscaled by
+// l_inv[rb * l_sr + k_first * l_sk] * u_inv[jb * u_sj + k_first * u_sk] with
+// rb = its 128-row block (rows past the last block, nrb, are not stored).
+// l_inv == nullptr: one scale for the whole product (*inv_scale_p).
+struct BlockScales {
+    const float *l_inv = nullptr, *u_inv = nullptr;
+    int l_sr = 0, l_sk = 0, u_sj = 0, u_sk = 0, nrb = 0, k_first = 0;
 };
 
 struct __align__(8) TcBarriers {
@@ -175,7 +189,7 @@ template <uint32_t FMT, int SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float *__restrict__ C, long ldc, int M, int N, int KB, int a_lo_row, int b_lo_row,
-                 const float *__restrict__ inv_scale_p, MpDevStatus *st, int lower) {
+                 const float *__restrict__ inv_scale_p, MpDevStatus *st, int lower, BlockScales bs) {
     constexpr int STAGES = TcCfg<SPLIT>::STAGES;
     constexpr int STAGE_BYTES = TcCfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smem_raw[];
@@ -228,11 +242,11 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     mbar_expect_tx(fb, STAGE_BYTES);
                     // stage layout: A_hi [A_lo] B_hi [B_lo]
                     constexpr int BKE = bk_elems<FMT>();
-                    tma_load_2d(sa, &mapA, kb * BKE, jb * TILE_J, fb);
-                    if (SPLIT == 2) tma_load_2d(sa + A_BYTES, &mapA, kb * BKE, a_lo_row + jb * TILE_J, fb);
-                    tma_load_2d(sa + SPLIT * A_BYTES, &mapB, kb * BKE, ib * TILE_I, fb);
-                    if (SPLIT == 2)
-                        tma_load_2d(sa + SPLIT * A_BYTES + B_BYTES, &mapB, kb * BKE, b_lo_row + ib * TILE_I, fb);
+                    const int kx = (bs.k_first + kb) * BKE;
+                    tma_load_2d(sa, &mapA, kx, jb * TILE_J, fb);
+                    if (SPLIT == 2) tma_load_2d(sa + A_BYTES, &mapA, kx, a_lo_row + jb * TILE_J, fb);
+                    tma_load_2d(sa + SPLIT * A_BYTES, &mapB, kx, ib * TILE_I, fb);
+                    if (SPLIT == 2) tma_load_2d(sa + SPLIT * A_BYTES + B_BYTES, &mapB, kx, b_lo_row + ib * TILE_I, fb);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -288,6 +302,15 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             tc_fence_after();
             const int col = jb * TILE_J + quarter * 32 + lane;
             const bool cval = col < N;
+            // per-block scales (E4M3): this K-block's scale of the tile's 128-row
+            // block of L21 times that of its 128-column block of U12
+            float tinv = inv_scale;
+            if (bs.l_inv) {
+                const int rb = 2 * ib + half;
+                tinv = rb < bs.nrb ? bs.l_inv[rb * bs.l_sr + bs.k_first * bs.l_sk] *
+                                         bs.u_inv[jb * bs.u_sj + bs.k_first * bs.u_sk]
+                                   : 0.f;
+            }
 #pragma unroll 1
             for (int ch = 0; ch < 4; ++ch) {
                 const int tcol = half * 128 + ch * 32;
@@ -300,7 +323,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * TILE_I + tcol, v);
 #pragma unroll
                 for (int r = 0; r < 32; ++r)
-                    if (cval && row0 + r < M) C[(long)(row0 + r) * ldc + col] = fmaf(-inv_scale, v[r], cv[r]);
+                    if (cval && row0 + r < M) C[(long)(row0 + r) * ldc + col] = fmaf(-tinv, v[r], cv[r]);
             }
             tc_fence_before();
             __syncwarp();
@@ -334,7 +357,7 @@ template <> __device__ __forceinline__ __nv_fp8_e4m3 to_half<__nv_fp8_e4m3>(floa
 template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
 pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long ldu, H *__restrict__ Ap, long lo_row,
-                      const float *__restrict__ scale) {
+                      const float *__restrict__ scale, const float *__restrict__ bscale = nullptr, int bs_stride = 0) {
     __shared__ float t[32][33];
     const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -349,7 +372,8 @@ pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long 
     for (int q = 0; q < 4; ++q) {
         const int j = j0 + ty + 8 * q, k = k0 + tx;
         if (j < N && k < Kpad) {
-            const float v = t[tx][ty + 8 * q] * sc;
+            // per-block scale of U's 128 x 128 block (k / 128, j / 128) when given
+            const float v = t[tx][ty + 8 * q] * (bscale ? bscale[(k >> 7) * bs_stride + (j >> 7)] : sc);
             const H hi = to_half<H>(v);
             Ap[(long)j * Kpad + k] = hi;
             if constexpr (SPLIT == 2) Ap[(lo_row + j) * Kpad + k] = to_half<H>(v - __half2float(hi));
@@ -362,14 +386,16 @@ pack_transpose_kernel(int K, int N, int Kpad, const float *__restrict__ U, long 
 template <typename H, int SPLIT>
 __global__ void __launch_bounds__(256)
 pack_rows_kernel(int M, int K, int Kpad, const float *__restrict__ L, long ldl, H *__restrict__ Bp, long lo_row,
-                 const float *__restrict__ scale) {
+                 const float *__restrict__ scale, const float *__restrict__ bscale = nullptr, int bs_stride = 0) {
     const float sc = (SPLIT == 2 || sizeof(H) == 1) ? *scale : 1.0f;
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M; i += gridDim.x * (blockDim.x >> 5)) {
         const float *src = L + (long)i * ldl;
         H *dst = Bp + (long)i * Kpad;
+        const float *brow = bscale ? bscale + (long)(i >> 7) * bs_stride : nullptr;
         for (int k = lane; k < Kpad; k += 32) {
-            const float v = (k < K ? src[k] : 0.f) * sc;
+            // per-block scale of the 128 x 128 block (i / 128, k / 128) when given
+            const float v = (k < K ? src[k] : 0.f) * (brow ? brow[k >> 7] : sc);
             const H hi = to_half<H>(v);
             dst[k] = hi;
             if constexpr (SPLIT == 2) dst[lo_row * Kpad + k] = to_half<H>(v - __half2float(hi));
@@ -418,6 +444,45 @@ __global__ void split_scales_kernel(const unsigned *umax_bits, const unsigned *l
     scales[0] = ldexpf(1.0f, el);
     scales[1] = ldexpf(1.0f, eu);
     scales[2] = ldexpf(1.0f, -el - eu);
+}
+
+// max |x| of every 128 x 128 block of a row-major rows x cols array into
+// out[rb * ncb + cb] (bits of a non-negative float; NaN as +inf).  One CTA per
+// block, consecutive threads along the block's rows (coalesced).
+__global__ void __launch_bounds__(256)
+block_absmax_kernel(int rows, int cols, const float *__restrict__ X, long ldx, unsigned *__restrict__ out, int ncb) {
+    __shared__ float wm[8];
+    const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
+    float m = 0.f;
+    for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+        const int r = r0 + (e >> 7), c = c0 + (e & 127);
+        if (r < rows && c < cols) {
+            const float v = fabsf(X[(long)r * ldx + c]);
+            m = (v > m || v != v) ? ((v != v) ? INFINITY : v) : m;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = wm[0];
+        for (int w = 1; w < 8; ++w) t = fmaxf(t, wm[w]);
+        out[blockIdx.y * ncb + blockIdx.x] = __float_as_uint(t);
+    }
+}
+
+// Per-block power-of-two scale 2^(top - e), max < 2^e (a zero or non-finite
+// block: 2^top), and its inverse; the rule of split_scales_kernel per block.
+__global__ void block_scales_kernel(int count, const unsigned *__restrict__ bits, float *__restrict__ scale,
+                                    float *__restrict__ inv, int top) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const float m = __uint_as_float(bits[i]);
+        int e = 0;
+        if (m > 0.f && m < INFINITY) frexpf(m, &e);
+        scale[i] = ldexpf(1.0f, top - e);
+        inv[i] = ldexpf(1.0f, e - top);
+    }
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -472,7 +537,12 @@ struct TcWs {
     void *Ap, *Bp;
     unsigned *umax;
     float *scales;
+    unsigned *lbits, *ubits;  // per-block maxima (E4M3)
+    float *lsc, *linv, *usc, *uinv;
 };
+
+// Blocks of 128 x 128 of an operand with `rows` rows and K columns.
+inline int blocks128(long v) { return (int)((v + 127) / 128); }
 
 // Scratch layout: [Ap: rowsA x Kpad][Bp: rowsB x Kpad][umax, scales]
 TcWs carve_ws(void *ws, int M, int N, int Kpad, int split, int esz) {
@@ -486,6 +556,14 @@ TcWs carve_ws(void *ws, int M, int N, int Kpad, int split, int esz) {
     p += align_up((size_t)rowsB * Kpad * esz, 1024);
     w.umax = reinterpret_cast<unsigned *>(p);
     w.scales = reinterpret_cast<float *>(p + 16);
+    p += 64;
+    const size_t nbl = (size_t)blocks128(std::max(M, N)) * blocks128(Kpad);
+    w.lbits = reinterpret_cast<unsigned *>(p);
+    w.ubits = w.lbits + nbl;
+    w.lsc = reinterpret_cast<float *>(w.ubits + nbl);
+    w.linv = w.lsc + nbl;
+    w.usc = w.linv + nbl;
+    w.uinv = w.usc + nbl;
     return w;
 }
 
@@ -506,7 +584,20 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     const long a_lo = SPLIT == 2 ? (long)(N + TILE_J - 1) / TILE_J * TILE_J : 0;
     const long b_lo = SPLIT == 2 ? (long)(M + TILE_I - 1) / TILE_I * TILE_I : 0;
     cudaError_t e;
-    if (SCALED) {
+    const int KBk = Kpad / BKE;  // K-blocks (128 wide for E4M3)
+    if (FMT == 2) {
+        // per-128 x 128-block scales of L21 and U12 (E4M3)
+        const int nrbL = blocks128(M), ncbU = blocks128(N);
+        mp_note_launch(2);
+        block_absmax_kernel<<<dim3(KBk, nrbL), 256, 0, s>>>(M, K, L21, ldl, w.lbits, KBk);
+        if (nt)
+            block_absmax_kernel<<<dim3(KBk, ncbU), 256, 0, s>>>(N, K, U12, ldu, w.ubits, KBk);
+        else
+            block_absmax_kernel<<<dim3(ncbU, KBk), 256, 0, s>>>(K, N, U12, ldu, w.ubits, ncbU);
+        mp_note_launch(2);
+        block_scales_kernel<<<(nrbL * KBk + 255) / 256, 256, 0, s>>>(nrbL * KBk, w.lbits, w.lsc, w.linv, 8);
+        block_scales_kernel<<<(ncbU * KBk + 255) / 256, 256, 0, s>>>(ncbU * KBk, w.ubits, w.usc, w.uinv, 8);
+    } else if (SCALED) {
         if (SPLIT == 2) {
             // the padding rows of both halves (up to the tile multiple) must be
             // zero; the pack kernels write every other element, K padding included
@@ -537,20 +628,22 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
                                             FMT == 2 ? 8 : 14);
     }
     {
+        const float *ubs = FMT == 2 ? w.usc : nullptr, *lbs = FMT == 2 ? w.lsc : nullptr;
         if (nt) {
             const long total = (long)N * Kpad;
             const int blocks = (int)std::min<long>((total + 255) / 256, 4L * 1024);
             mp_note_launch();
-            pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(N, K, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
+            pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(N, K, Kpad, U12, ldu, Ap, a_lo, w.scales + 1, ubs, KBk);
         } else {
             dim3 grid((N + 31) / 32, (Kpad + 31) / 32);
             mp_note_launch();
-            pack_transpose_kernel<H, SPLIT><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap, a_lo, w.scales + 1);
+            pack_transpose_kernel<H, SPLIT><<<grid, 256, 0, s>>>(K, N, Kpad, U12, ldu, Ap, a_lo, w.scales + 1, ubs,
+                                                                 blocks128(N));
         }
         const long total = (long)M * Kpad;
         const int blocks = (int)std::min<long>((total + 255) / 256, 4L * 1024);
         mp_note_launch();
-        pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(M, K, Kpad, L21, ldl, Bp, b_lo, w.scales);
+        pack_rows_kernel<H, SPLIT><<<blocks, 256, 0, s>>>(M, K, Kpad, L21, ldl, Bp, b_lo, w.scales, lbs, KBk);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -565,9 +658,27 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     if (e != cudaSuccess) return e;
     const int ntiles = ((M + TILE_I - 1) / TILE_I) * ((N + TILE_J - 1) / TILE_J);
     const int grid = std::min(ntiles, num_sms());
+    if (FMT == 2) {
+        // one launch per K-block: each block's products carry their own scales
+        BlockScales bs;
+        bs.l_inv = w.linv;
+        bs.l_sr = KBk;
+        bs.l_sk = 1;
+        bs.u_inv = w.uinv;
+        bs.u_sj = nt ? KBk : 1;
+        bs.u_sk = nt ? 1 : blocks128(N);
+        bs.nrb = blocks128(M);
+        for (int kb = 0; kb < KBk; ++kb) {
+            bs.k_first = kb;
+            mp_note_launch();
+            kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, 1, (int)a_lo, (int)b_lo, w.scales + 2, st,
+                                                 lower, bs);
+        }
+        return cudaGetLastError();
+    }
     mp_note_launch();
-    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, Kpad / BKE, (int)a_lo, (int)b_lo,
-                                         w.scales + 2, st, lower);
+    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, KBk, (int)a_lo, (int)b_lo, w.scales + 2, st,
+                                         lower, BlockScales{});
     return cudaGetLastError();
 }
 
@@ -603,7 +714,9 @@ size_t tc_workspace_bytes(int n, int nb, int prec) {
     const int split = prec == MP_PREC_FP16X3 ? 2 : 1;
     const size_t rowsA = split == 2 ? 2 * ((size_t)(n + TILE_J - 1) / TILE_J * TILE_J) : (size_t)n;
     const size_t rowsB = split == 2 ? 2 * ((size_t)(n + TILE_I - 1) / TILE_I * TILE_I) : (size_t)n;
-    return align_up(rowsA * kpad * 2, 1024) + align_up(rowsB * kpad * 2, 1024) + 1024;
+    // + the E4M3 per-block maxima, scales and inverses (6 arrays of 4 bytes per block)
+    const size_t nbl = (size_t)((n + 127) / 128) * ((kpad + 127) / 128);
+    return align_up(rowsA * kpad * 2, 1024) + align_up(rowsB * kpad * 2, 1024) + 1024 + 24 * nbl;
 }
 
 cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, long ldl, const float *U12,
