@@ -603,6 +603,44 @@ def run_fig4(args):
     return 0
 
 
+def run_dd(args):
+    """Section 5's experiment on the GPU (Tables 6 and 7): refinement with an
+    extra-precise residual (double-double here, quadruple precision in the
+    paper) on FP64 factors, for uniform random matrices of order 100 .. 1000
+    and 4096.  Per n: the time of mp_gesv_dd (median of 3 after a warm-up),
+    its corrections, the FP64 solve's time for reference, and, at n = 900
+    (the paper's Table 7 size), the time by phase: conversion and norms,
+    FP64 LU (DGETRF), the FP64 triangular solves (DGETRS), the
+    double-double residual (the QGEMV step) and the whole refinement loop."""
+    import torch
+    from paper_0808_2794_gb300 import solver
+    torch.cuda.set_device(0)
+    rows = []
+    for n in list(range(100, 1001, 100)) + [4096]:
+        rng = np.random.default_rng(n)
+        A = torch.from_numpy(np.asfortranarray(rng.uniform(-1.0, 1.0, (n, n)))).cuda()
+        b = torch.from_numpy(rng.uniform(-1.0, 1.0, n)).cuda()
+        solver.gesv_dd(A, b)
+        ms, (xh, xl, _, st) = _cuda_ms(torch, lambda: solver.gesv_dd(A, b), 3)
+        solver.gesv(A, b, prec="fp64")
+        ms64, _ = _cuda_ms(torch, lambda: solver.gesv(A, b, prec="fp64"), 3)
+        row = {"n": n, "ms_dd": ms, "ms_fp64_solve": ms64, "corrections": st["iter"], "flags": st["flags"]}
+        if n == 900:
+            solver.profile_enable(solver.KERNEL_CLASSES)
+            _, _, _, st2 = solver.gesv_dd(A, b)
+            torch.cuda.synchronize()
+            prof = solver.profile_collect()
+            solver.profile_enable(())
+            row["phases_ms"] = {"convert_and_norms": st2["ms_convert"], "fp64_lu": st2["ms_factor"],
+                                "refinement_loop": st2["ms_refine"], "fp64_triangular_solves": prof["trsv"][0],
+                                "dd_residual": prof["residual"][0]}
+        rows.append(row)
+    line = {"metric": "Section 5 (QDGESV analogue): double-double refinement on FP64 factors, ms per solve",
+            "workload": "uniform (-1, 1) random matrices, nrhs = 1", "table": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,7 +652,7 @@ def main():
     ap.add_argument("--prec", default="fp16x3")
     ap.add_argument("--refine", default="classical", choices=["classical", "gmres", "auto"])
     ap.add_argument("--fig4-count", type=int, default=200)
-    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint", "fig4"],
+    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint", "fig4", "dd"],
                     help="lu: the headline dense solve; the others time the secondary "
                          "workloads (SPD Cholesky, batched small systems, adjoint solve)")
     ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
@@ -630,6 +668,8 @@ def main():
         return run_reference(args)
     if args.workload == "fig4":
         return run_fig4(args)
+    if args.workload == "dd":
+        return run_dd(args)
     if args.workload != "lu":
         return run_secondary(args)
 

@@ -196,6 +196,53 @@ MP_API int mp_gesv_batched(int batch, const int *n, const int *nrhs, const doubl
 MP_API int mp_batched_set_schedule(int count, const int *nmax, const int *nb);
 MP_API int mp_batched_get_schedule(int cap, int *count, int *nmax, int *nb);
 
+/* Solve A X = B to more than FP64 accuracy by refinement with an
+ * extra-precise residual (Section 5, QDGESV: an FP64 LU factorization, then
+ * iterative refinement whose residual b - A x is computed, and whose solution
+ * is kept, in a precision beyond FP64; Tables 6 and 7).  Here the extended
+ * precision is double-double: X is returned as the unevaluated sum
+ * Xhi + Xlo of two FP64 arrays (|Xlo| <= ulp(Xhi)/2).  A (n x n) and B
+ * (n x nrhs) are FP64 column-major DEVICE arrays read as exact values; the
+ * factorization is FP64 LU with partial pivoting (dipiv: n int32, LAPACK
+ * 1-based, output); x_0 is the FP64 solve and each step computes
+ * r = b - A (xhi + xlo) accumulated in double-double (error-free
+ * two-products and two-sums, rounded to FP64 at the end), solves for z with
+ * the FP64 factors and adds it in double-double.  A column stops when its
+ * last correction is below 2^-100 ||x||inf or stopped shrinking (||z_k|| >
+ * ||z_{k-1}|| / 2 for k >= 2: the limiting accuracy), the loop at itermax
+ * corrections (MP_FLAG_NOT_CONVERGED).  stats (optional): iter = corrections,
+ * hist/bwd_err = the FP64 normwise backward error of each residual,
+ * ms_convert / ms_factor / ms_refine = phase times.  Returns 0, -i for an
+ * illegal argument i (1..15), +i for an exact zero pivot U(i,i) (A singular;
+ * X is not computed), or a CUDA error (<= -1000).  work: DEVICE scratch of
+ * mp_gesv_dd_workspace_bytes(n, nrhs) bytes. */
+MP_API size_t mp_gesv_dd_workspace_bytes(int n, int nrhs);
+MP_API int mp_gesv_dd(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dXhi,
+                      double *dXlo, int ldx, int32_t *dipiv, int itermax, void *work, size_t work_bytes,
+                      mp_stats *stats, void *stream);
+
+/* Linear least squares min ||b - A x||_2 for A m x n (m >= n, full column
+ * rank) by mixed-precision refinement of the augmented system (Section 6
+ * names least squares among the algorithms the approach extends to; the
+ * augmented formulation is Bjorck's):
+ *     [ alpha I   A ] [ r / alpha ]   [ b ]
+ *     [ A^T       0 ] [ x         ] = [ 0 ]
+ * The (m + n)-order system is built in the workspace and solved by mp_gesv
+ * with opts (low-precision LU with partial pivoting, FP64 residual and
+ * refinement, FP64 fallback), which gives x and the residual r = b - A x in
+ * FP64.  alpha: a power of two (exact scaling), 0 = automatic (the power of
+ * two nearest ||A||_F / sqrt(8 n), about sigma_min / sqrt(2) for a
+ * well-conditioned A, where the augmented matrix's condition number is about
+ * 2 kappa_2(A)).  dA: m x n, dB: m x nrhs, dX: n x nrhs, dR (optional, NULL
+ * to skip): m x nrhs, all FP64 column-major DEVICE arrays.  stats: those of
+ * the augmented solve.  Returns 0, -i for an illegal argument i (1..17), +i
+ * when the FP64 factorization of the augmented matrix met a zero pivot
+ * (A rank deficient), or a CUDA error (<= -1000).  m + n <= 65536. */
+MP_API size_t mp_gels_workspace_bytes(int m, int n, int nrhs, const mp_opts *opts);
+MP_API int mp_gels(int m, int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX,
+                   int ldx, double *dR, int ldr, double alpha, void *work, size_t work_bytes, const mp_opts *opts,
+                   mp_stats *stats, void *stream);
+
 /* Adjoint of the solve (reverse-mode derivative of X = A^{-1} B; the paper
  * has no counterpart).  Given the FP64 cotangent G = dL/dX (n x nrhs),
  * computes Bbar = A^{-T} G (n x nrhs) and Abar = -Bbar X^T (n x n, FP64,

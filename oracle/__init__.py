@@ -79,6 +79,7 @@ def _load():
                 "or_bwd_err": (None, [I, I, P, I, P, I, P, I, P]),
                 "or_gesv_ir": (I, [I, I, P, I, P, I, P, I, I, I, D, D, I, P, P, P, P, P]),
                 "or_posv_ir": (I, [I, I, P, I, P, I, P, I, I, I, D, D, I, P, P, P]),
+                "or_gesv_dd": (I, [I, I, P, I, P, I, P, P, I, I, P]),
                 "or_kappa_inf": (D, [I, P, I]),
                 "or_kappa_1_est": (D, [I, P, I]),
                 "or_dinvnorm1_est_lu": (D, [I, P, I, P, I]),
@@ -245,6 +246,46 @@ def gesv_ir(A, B, factor_prec: int = 32, itermax: int = 30, tol: float = 1e-14,
                           ctypes.byref(bw), ctypes.byref(nh), _p(hist))
     return dict(X=X[:, 0] if squeeze else X, info=info, iter=it.value, flags=fl.value,
                 bwd=bw.value, hist=hist[:nh.value].copy())
+
+
+def gesv_dd(A, B, itermax: int = 10):
+    """Section 5's extra-precise refinement with FP64 factors: returns
+    dict(Xhi, Xlo, info, iter) with X = Xhi + Xlo in double-double."""
+    lib = _load()
+    Af = _f(A, np.float64)
+    squeeze = np.asarray(B).ndim == 1
+    Bf = _f(B, np.float64)
+    n, nrhs = Bf.shape
+    Xh = np.zeros((n, nrhs), dtype=np.float64, order="F")
+    Xl = np.zeros((n, nrhs), dtype=np.float64, order="F")
+    it = ctypes.c_int(0)
+    info = lib.or_gesv_dd(n, nrhs, _p(Af), max(n, 1), _p(Bf), max(n, 1), _p(Xh), _p(Xl), max(n, 1),
+                          int(itermax), ctypes.byref(it))
+    if squeeze:
+        Xh, Xl = Xh[:, 0], Xl[:, 0]
+    return dict(Xhi=Xh, Xlo=Xl, info=info, iter=it.value)
+
+
+def gels_aug(A, B, alpha: float = 0.0):
+    """Least squares min ||b - A x||_2 (Section 6's extension) through the
+    augmented system [alpha I, A; A^T, 0] [r / alpha; x] = [b; 0], solved by
+    the oracle's Algorithm 1 with FP64 factors; alpha = 0 picks the power of
+    two nearest ||A||_F / sqrt(8 n).  Returns dict(X, R, alpha, info)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    Bm = np.asarray(B, dtype=np.float64).reshape(m, -1)
+    if alpha == 0.0:
+        t = float(np.sqrt(np.sum(A * A) / (8.0 * n)))
+        alpha = 2.0 ** int(round(np.log2(t))) if t > 0 else 1.0
+    K = np.zeros((m + n, m + n))
+    K[:m, :m] = alpha * np.eye(m)
+    K[:m, m:] = A
+    K[m:, :m] = A.T
+    F = np.zeros((m + n, Bm.shape[1]))
+    F[:m] = Bm
+    r = gesv_ir(np.asfortranarray(K), np.asfortranarray(F), factor_prec=64)
+    Y = r["X"].reshape(m + n, -1)
+    return dict(X=Y[m:], R=alpha * Y[:m], alpha=alpha, info=r["info"])
 
 
 def posv_ir(A, B, factor_prec: int = 32, itermax: int = 30, tol: float = 1e-14,

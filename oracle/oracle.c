@@ -33,6 +33,8 @@
  *   kappa_inf_exact, kappa_1_est,       : pinned (Hilbert / tridiagonal closed forms;
  *   dinvnorm1_est_lu                      lower bound within 10x of the exact norm)
  *   gmres_ir                            : pinned (special cases, exact solve bound)
+ *   gesv_dd                             : pinned (exact rational solves, including a
+ *                                         floating-point Hilbert matrix, kappa ~ 1e13)
  *   round_bf16/fp16/e4m3                : pinned (enumerated representable values)
  */
 #include <math.h>
@@ -768,6 +770,88 @@ int or_posv_ir(int n, int nrhs, const double *A, int lda, const double *B,
 
 /* kappa_inf(A) = ||A||_inf ||A^{-1}||_inf with A^{-1} formed column by
  * column from an FP64 LU (n solves).  Returns +inf if A is singular. */
+/* ------------------------------------------------------------------ */
+/* Iterative refinement with an extra-precise residual (Section 5,      */
+/* QDGESV): FP64 LU with partial pivoting, x_0 from it, then           */
+/*   r = b - A x   with x = xhi + xlo and the sum carried in            */
+/*                 double-double (two-products and two-sums, columns in  */
+/*                 order), rounded to FP64,                              */
+/*   z = (LU)^{-1} P r in FP64,                                          */
+/*   x = x + z     in double-double (two-sum, renormalised),             */
+/* until the last correction is below 2^-100 ||x||inf or stopped         */
+/* shrinking (||z_k|| > ||z_{k-1}|| / 2 for k >= 2), at most itermax     */
+/* corrections.  Returns info of the LU (> 0: singular); *iter_out the   */
+/* corrections applied (-1 when itermax was reached first).             */
+/* ------------------------------------------------------------------ */
+int or_gesv_dd(int n, int nrhs, const double *A, int lda, const double *B, int ldb,
+               double *Xhi, double *Xlo, int ldx, int itermax, int *iter_out) {
+    size_t nn = (size_t)n * (size_t)n;
+    double *F = (double *)malloc(sizeof(double) * (nn ? nn : 1));
+    int *ipiv = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) F[IDX(i, j, n)] = A[IDX(i, j, lda)];
+    const int info = or_dgetrf(n, F, n, ipiv);
+    int worst_iter = 0;
+    if (info == 0) {
+        for (int c = 0; c < nrhs; ++c) {
+            double *xh = &Xhi[IDX(0, c, ldx)], *xl = &Xlo[IDX(0, c, ldx)];
+            const double *b = &B[IDX(0, c, ldb)];
+            for (int i = 0; i < n; ++i) { xh[i] = b[i]; xl[i] = 0.0; }
+            or_dgetrs(n, 1, F, n, ipiv, xh, n);
+            double zprev = 0.0, znorm = 0.0;
+            for (int i = 0; i < n; ++i) znorm = fmax(znorm, fabs(xh[i]));
+            int it = 0;
+            for (;;) {
+                double xnorm = 0.0;
+                for (int i = 0; i < n; ++i) xnorm = fmax(xnorm, fabs(xh[i]));
+                /* r = b - A (xh + xl): double-double sum of the products */
+                double rnorm = 0.0;
+#pragma omp parallel for schedule(static) if (n > 256)
+                for (int i = 0; i < n; ++i) {
+                    double s = 0.0, comp = 0.0;
+                    for (int j = 0; j < n; ++j) {
+                        double p, ep, t, es;
+                        two_prod(A[IDX(i, j, lda)], xh[j], &p, &ep);
+                        two_sum(s, p, &t, &es);
+                        s = t;
+                        comp += ep + es;
+                        comp = fma(A[IDX(i, j, lda)], xl[j], comp);
+                    }
+                    double d, e;
+                    two_sum(b[i], -s, &d, &e);
+                    r[i] = d + (e - comp);
+                }
+                for (int i = 0; i < n; ++i) rnorm = fmax(rnorm, fabs(r[i]));
+                const int done = rnorm == 0.0 || znorm <= ldexp(1.0, -100) * xnorm ||
+                                 (it >= 2 && znorm > 0.5 * zprev);
+                if (done) break;
+                if (it >= itermax) { it = -1; break; }
+                or_dgetrs(n, 1, F, n, ipiv, r, n);
+                zprev = znorm;
+                znorm = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    double s, e;
+                    two_sum(xh[i], r[i], &s, &e);
+                    e += xl[i];
+                    const double h = s + e;
+                    xh[i] = h;
+                    xl[i] = e - (h - s);
+                    znorm = fmax(znorm, fabs(r[i]));
+                }
+                ++it;
+            }
+            if (it < 0) worst_iter = -1;                        /* a column hit itermax */
+            else if (worst_iter >= 0 && it > worst_iter) worst_iter = it;
+        }
+    }
+    if (iter_out) *iter_out = worst_iter;
+    free(F);
+    free(ipiv);
+    free(r);
+    return info;
+}
+
 double or_kappa_inf(int n, const double *A, int lda) {
     size_t nn = (size_t)n * (size_t)n;
     double *F = (double *)malloc(sizeof(double) * (nn ? nn : 1));

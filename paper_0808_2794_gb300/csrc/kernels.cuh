@@ -215,3 +215,15 @@ cudaError_t launch_selftest_grid_barrier(unsigned *bar, MpDevStatus *st, unsigne
 cudaError_t launch_selftest_panel_mbar(MpDevStatus *st, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_selftest_tc_mbar(MpDevStatus *st, const int *abort_flag, unsigned long long limit_ns,
                                     cudaStream_t s);
+
+// ---- extra-precise refinement (dd.cu) ------------------------------------------
+// Column chunks of the double-double residual (part arrays: ksplit x nrhs x n each).
+int residual_dd_ksplit(int n);
+// R = fl64(B - A (Xhi + Xlo)) with the residual accumulated in double-double;
+// rnorm/xnorm (zeroed by the caller) = max |R|, max |Xhi| per column.
+cudaError_t launch_residual_dd(int n, int nrhs, const double *A, long lda, const double *Xhi, const double *Xlo,
+                               long ldx, const double *B, long ldb, double *part_hi, double *part_lo, int ksplit,
+                               double *R, long ldr, double *rnorm, double *xnorm, cudaStream_t s);
+// (Xhi, Xlo) += s Z (or := s Z when assign), s = 2^ceil(log2 rnorm); znorm = max |s Z| (zeroed by the caller).
+cudaError_t launch_update_dd(int n, int nrhs, const double *Z, long ldz, const double *rnorm, double *Xhi,
+                             double *Xlo, long ldx, double *znorm, int assign, cudaStream_t s);

@@ -1686,3 +1686,134 @@ extern "C" int mp_selftest_wait_timeout(int site, unsigned long long limit_ns, v
     if (passed) *passed = hp;
     return 0;
 }
+
+// ---------------------------------------------------------------------------
+// extra-precise refinement (Section 5: QDGESV)
+// ---------------------------------------------------------------------------
+namespace {
+mp_opts dd_opts() {
+    mp_opts o;
+    mp_default_opts(&o);
+    o.prec = MP_PREC_FP64;
+    return o;
+}
+size_t dd_part_bytes(int n, int nrhs) {
+    return (size_t)residual_dd_ksplit(std::max(n, 1)) * (size_t)std::max(n, 1) * (size_t)std::max(nrhs, 1) *
+           sizeof(double);
+}
+}  // namespace
+
+extern "C" size_t mp_gesv_dd_workspace_bytes(int n, int nrhs) {
+    if (n < 0 || nrhs < 0) return 0;
+    const mp_opts o = dd_opts();
+    return make_layout(n, nrhs, o, true).total + 2 * align_up(dd_part_bytes(n, nrhs), 256);
+}
+
+extern "C" int mp_gesv_dd(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dXhi,
+                          double *dXlo, int ldx, int32_t *dipiv, int itermax, void *work, size_t work_bytes,
+                          mp_stats *stats, void *stream) {
+    g_err[0] = 0;
+    if (n < 0) return mp_arg_fail(1, "n < 0");
+    if (nrhs < 0 || nrhs > kMaxRhs) return mp_arg_fail(2, "nrhs must be in [0, 8]");
+    if (n > 65536) return mp_arg_fail(1, "n > 65536 is not supported");
+    if (n > 0 && !dA) return mp_arg_fail(3, "A is NULL");
+    if (lda < std::max(1, n)) return mp_arg_fail(4, "lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dB) return mp_arg_fail(5, "B is NULL");
+    if (ldb < std::max(1, n)) return mp_arg_fail(6, "ldb < max(1, n)");
+    if (n > 0 && nrhs > 0 && !dXhi) return mp_arg_fail(7, "Xhi is NULL");
+    if (n > 0 && nrhs > 0 && !dXlo) return mp_arg_fail(8, "Xlo is NULL");
+    if (ldx < std::max(1, n)) return mp_arg_fail(9, "ldx < max(1, n)");
+    if (n > 0 && !dipiv) return mp_arg_fail(10, "ipiv is NULL");
+    if (itermax < 0) return mp_arg_fail(11, "itermax < 0");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n == 0 || nrhs == 0) return 0;
+    const mp_opts o = dd_opts();
+    Layout L = make_layout(n, nrhs, o, true);
+    if (!work) return mp_arg_fail(12, "workspace is NULL");
+    if (work_bytes < mp_gesv_dd_workspace_bytes(n, nrhs)) return mp_arg_fail(13, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *part_hi = at<double>(work, L.total);
+    double *part_lo = at<double>(work, L.total + align_up(dd_part_bytes(n, nrhs), 256));
+    const int ks = residual_dd_ksplit(n);
+    Solve S{n, nrhs, dA, lda, dB, ldb, dXhi, ldx, work, L, s, at<StatusBlock>(work, L.status), 0, false};
+    const bool timing = stats != nullptr;
+    cudaEvent_t ev[4] = {};
+    if (timing)
+        for (auto &e : ev) MP_CUDA_TRY(cudaEventCreate(&e));
+    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+    mark(0);
+    MP_CUDA_TRY(cudaMemsetAsync(S.sb, 0, sizeof(StatusBlock), s));
+    MP_CUDA_TRY(cudaMemsetAsync(at<double>(work, L.rowsum), 0, sizeof(double) * n, s));
+    if (reset_sync(S)) return -1000;
+    MP_CUDA_TRY(launch_convert_transpose<double>(n, dA, lda, at<double>(work, L.W), L.ldw, at<double>(work, L.rowsum),
+                                                 &S.sb->st, s));
+    MP_CUDA_TRY(launch_max_reduce(n, at<double>(work, L.rowsum), &S.sb->st.anorm, s));
+    MP_CUDA_TRY(launch_col_absmax(n, nrhs, dB, ldb, S.sb->bnorm, &S.sb->st, s));
+    mark(1);
+    int info = 0, e;
+    uint32_t fflags = 0, flags = 0;
+    if ((e = factor<double>(S, MP_PREC_FP32, std::min(L.nb, 256), &info, &fflags))) return e;
+    mark(2);
+    flags |= fflags & MP_FLAG_NONFINITE_INPUT;
+    MP_CUDA_TRY(cudaMemcpyAsync(dipiv, at<int32_t>(work, L.ipiv), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    int it = 0;
+    if (info == 0 && !(flags & MP_FLAG_NONFINITE_INPUT)) {
+        // x_0 = (LU)^{-1} P b in FP64, x_lo = 0
+        MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, s));
+        if ((e = lowp_solve<double>(S, dB, ldb, S.sb->bnorm, nrhs))) return e;
+        MP_CUDA_TRY(launch_update_dd(n, nrhs, at<double>(work, L.Z), n, S.sb->bnorm, dXhi, dXlo, ldx, S.sb->znorm, 1, s));
+        double zprev[kMaxRhs] = {0};
+        const double floor = std::ldexp(1.0, -100);
+        for (;;) {
+            // r = b - A (x_hi + x_lo) accumulated in double-double, rounded to FP64
+            MP_CUDA_TRY(cudaMemsetAsync(S.sb->rnorm, 0, sizeof(double) * 2 * kMaxRhs, s));
+            {
+                MpProfScope ps(MP_KC_RESIDUAL, 8.0 * n * n + 24.0 * n * nrhs, s);
+                MP_CUDA_TRY(launch_residual_dd(n, nrhs, dA, lda, dXhi, dXlo, ldx, dB, ldb, part_hi, part_lo, ks,
+                                               at<double>(work, L.R), n, S.sb->rnorm, S.sb->xnorm, s));
+            }
+            StatusBlock h;
+            if ((e = read_status(S, h))) return e;
+            // a column is done when its last correction reached the
+            // double-double floor or stopped shrinking (the accuracy the
+            // residual allows); the loop also ends at itermax corrections
+            bool done = true, nonfinite = false;
+            double worst = 0.0;
+            for (int c = 0; c < nrhs; ++c) {
+                const double den = h.st.anorm * h.xnorm[c] + h.bnorm[c];
+                const double b = den > 0.0 ? h.rnorm[c] / den : (h.rnorm[c] > 0.0 ? INFINITY : 0.0);
+                worst = std::max(worst, std::isnan(b) ? INFINITY : b);
+                if (!std::isfinite(h.rnorm[c]) || !std::isfinite(h.xnorm[c])) nonfinite = true;
+                const bool c_done = h.rnorm[c] == 0.0 || h.znorm[c] <= floor * h.xnorm[c] ||
+                                    (it >= 2 && h.znorm[c] > 0.5 * zprev[c]);
+                if (!c_done) done = false;
+            }
+            if (stats) {
+                if (stats->nhist < 32) stats->hist[stats->nhist++] = worst;
+                stats->bwd_err = worst;
+            }
+            if (nonfinite) { flags |= MP_FLAG_LOWP_BREAKDOWN; break; }
+            if (done) break;
+            if (it >= itermax) { flags |= MP_FLAG_NOT_CONVERGED; break; }
+            std::memcpy(zprev, h.znorm, sizeof zprev);
+            if ((e = lowp_solve<double>(S, at<double>(work, L.R), n, S.sb->rnorm, nrhs))) return e;
+            MP_CUDA_TRY(cudaMemsetAsync(S.sb->znorm, 0, sizeof(double) * kMaxRhs, s));
+            MP_CUDA_TRY(launch_update_dd(n, nrhs, at<double>(work, L.Z), n, S.sb->rnorm, dXhi, dXlo, ldx, S.sb->znorm,
+                                         0, s));
+            ++it;
+        }
+    }
+    mark(3);
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iter = it;
+        stats->flags = flags;
+        stats->info = info;
+        cudaEventElapsedTime(&stats->ms_convert, ev[0], ev[1]);
+        cudaEventElapsedTime(&stats->ms_factor, ev[1], ev[2]);
+        cudaEventElapsedTime(&stats->ms_refine, ev[2], ev[3]);
+    }
+    if (timing)
+        for (auto &x : ev) cudaEventDestroy(x);
+    return info;
+}

@@ -92,6 +92,11 @@ _SIGS = {
                              ctypes.POINTER(mp_stats), _P]),
     "mp_batched_set_schedule": (_I, [_I, _P, _P]),
     "mp_batched_get_schedule": (_I, [_I, ctypes.POINTER(ctypes.c_int), _P, _P]),
+    "mp_gesv_dd_workspace_bytes": (_Z, [_I, _I]),
+    "mp_gesv_dd": (_I, [_I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _I, _P, _Z, ctypes.POINTER(mp_stats), _P]),
+    "mp_gels_workspace_bytes": (_Z, [_I, _I, _I, ctypes.POINTER(mp_opts)]),
+    "mp_gels": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, ctypes.c_double, _P, _Z, ctypes.POINTER(mp_opts),
+                     ctypes.POINTER(mp_stats), _P]),
     "mp_selftest_workspace_bytes": (_Z, []),
     "mp_selftest_wait_timeout": (_I, [_I, ctypes.c_ulonglong, _P, _Z, ctypes.POINTER(ctypes.c_uint),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
@@ -621,3 +626,60 @@ def set_batched_schedule(entries=None):
     nm = np.array([e[0] for e in entries], dtype=np.int32)
     nb = np.array([e[1] for e in entries], dtype=np.int32)
     _check(lib.mp_batched_set_schedule(len(entries), nm.ctypes.data, nb.ctypes.data), "mp_batched_set_schedule")
+
+
+def gesv_dd(A, B, itermax=10, work=None, stream=None):
+    """Solve A X = B to double-double accuracy (Section 5's extra-precise
+    refinement with FP64 factors).  A: (n, n) float64 CUDA tensor, B: (n,) or
+    (n, nrhs).  Returns (Xhi, Xlo, ipiv, stats) with X = Xhi + Xlo."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = B.dim() == 1
+    B = colmajor(B)
+    n, nrhs = B.shape
+    Xhi = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    Xlo = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    need = lib.mp_gesv_dd_workspace_bytes(n, nrhs)
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    st = mp_stats()
+    ret = lib.mp_gesv_dd(n, nrhs, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), Xhi.data_ptr(), Xlo.data_ptr(),
+                         _ld(Xhi), ipiv.data_ptr(), int(itermax), work.data_ptr(), work.numel(), ctypes.byref(st),
+                         _stream_ptr(stream))
+    _check(ret, "mp_gesv_dd")
+    d = st.as_dict()
+    d["info_fp64"] = ret
+    if squeeze:
+        return Xhi[:, 0], Xlo[:, 0], ipiv[:n], d
+    return Xhi, Xlo, ipiv[:n], d
+
+
+def gels(A, B, prec="fp32", refine="classical", alpha=0.0, allow_fallback=True, work=None, stream=None):
+    """Least squares min ||B - A X||_2 (A: (m, n) float64 CUDA tensor, m >= n,
+    full column rank; B: (m,) or (m, nrhs)) by refinement of the augmented
+    system.  Returns (X, R, stats) with R = B - A X."""
+    torch = _torch()
+    lib = load()
+    A = colmajor(A)
+    squeeze = B.dim() == 1
+    B = colmajor(B)
+    m, n = A.shape
+    nrhs = B.shape[1]
+    opts = default_opts(prec=prec, refine=refine, allow_fallback=int(bool(allow_fallback)))
+    X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    R = torch.empty((nrhs, m), dtype=torch.float64, device=A.device).t()
+    need = lib.mp_gels_workspace_bytes(m, n, nrhs, ctypes.byref(opts))
+    if work is None or work.numel() < need:
+        work = workspace(need, A.device)
+    st = mp_stats()
+    ret = lib.mp_gels(m, n, nrhs, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), R.data_ptr(),
+                      _ld(R), float(alpha), work.data_ptr(), work.numel(), ctypes.byref(opts), ctypes.byref(st),
+                      _stream_ptr(stream))
+    _check(ret, "mp_gels")
+    d = st.as_dict()
+    d["info_fp64"] = ret
+    if squeeze:
+        return X[:, 0], R[:, 0], d
+    return X, R, d

@@ -450,3 +450,112 @@ def test_round_e4m3_brute_force(orc):
     for x in xs:
         want = 448.0 if x > 448.0 else _brute_nearest(x, grid)
         assert orc.round_to([x], "e4m3")[0] == want
+
+
+# ----------------------------------- extra-precise refinement (Section 5)
+
+UDD = 2.0 ** -104
+
+
+def _dd_frac(xh, xl):
+    return [Fraction(float(h)) + Fraction(float(l)) for h, l in zip(xh, xl)]
+
+
+@pytest.mark.parametrize("n", [2, 5, 8])
+@pytest.mark.parametrize("seed", range(3))
+def test_gesv_dd_matches_exact_solve(orc, n, seed):
+    """FP64 factors, double-double residual and solution: the result
+    Xhi + Xlo equals the exact rational solution to within the double-double
+    level kappa u_dd (far below FP64's kappa u64)."""
+    A = inputs.small_integer_matrix(n, seed=500 + 10 * n + seed, lo=-99, hi=99)
+    A[np.diag_indices(n)] += 150.0
+    b = np.array([1.0 / 3.0 + i for i in range(n)])  # not exactly representable in binary
+    Af = exact.to_frac_matrix(A.tolist())
+    x_ex = exact.solve(Af, [Fraction(v) for v in b])
+    kappa = float(exact.norm_inf(Af) * exact.norm_inf(exact.inverse(Af)))
+    r = orc.gesv_dd(A, b)
+    assert r["info"] == 0 and r["iter"] >= 1
+    x = _dd_frac(r["Xhi"], r["Xlo"])
+    xm = max(abs(v) for v in x_ex)
+    err = max(abs(a - e) for a, e in zip(x, x_ex))
+    assert err <= 64 * n * kappa * UDD * xm, (float(err), float(xm))
+
+
+def test_gesv_dd_on_floating_point_hilbert_matrix(orc):
+    """The FP64 Hilbert matrix of order 10 (kappa ~ 1.6e13): the FP64 solve
+    alone keeps about three digits; refinement with the double-double
+    residual reaches the exact rational solution of that matrix to well
+    below FP64's unit roundoff."""
+    n = 10
+    A = np.array([[1.0 / (i + j + 1) for j in range(n)] for i in range(n)], order="F")
+    b = np.ones(n)
+    Af = exact.to_frac_matrix(A.tolist())
+    x_ex = exact.solve(Af, [Fraction(1)] * n)
+    xm = max(abs(v) for v in x_ex)
+    r = orc.gesv_dd(A, b, itermax=20)
+    assert r["info"] == 0 and r["iter"] >= 2
+    err = max(abs(a - e) for a, e in zip(_dd_frac(r["Xhi"], r["Xlo"]), x_ex))
+    assert err <= 1e-16 * xm, float(err / xm)
+    LU, piv, _ = orc.getrf(A)
+    x0 = orc.getrs(LU, piv, b)
+    err0 = max(abs(Fraction(float(a)) - e) for a, e in zip(x0, x_ex))
+    assert err0 >= 1e-8 * xm  # the FP64 solve by itself is far less accurate
+
+
+def test_gesv_dd_integer_system_exact(orc):
+    """Integer A and integer x_true (b = A x_true exact in FP64): the
+    double-double solution is x_true to within double-double rounding."""
+    n = 40
+    rng = np.random.default_rng(9)
+    A = np.asfortranarray(rng.integers(-20, 21, (n, n)).astype(np.float64))
+    A[np.diag_indices(n)] += 100.0
+    xt = rng.integers(-1000, 1001, (n, 2)).astype(np.float64)
+    B = A @ xt  # integers below 2^53: exact
+    r = orc.gesv_dd(A, B)
+    assert r["info"] == 0
+    for c in range(2):
+        for i in range(n):
+            assert abs(Fraction(float(r["Xhi"][i, c])) + Fraction(float(r["Xlo"][i, c])) - int(xt[i, c])) \
+                <= Fraction(1, 10 ** 20) * 1000
+
+
+# ------------------------------------------- least squares (Section 6 extension)
+
+def _ls_exact(A, b):
+    """Exact rational least-squares solution from the normal equations."""
+    Af = exact.to_frac_matrix(A.tolist())
+    m, n = len(Af), len(Af[0])
+    AtA = [[sum(Af[k][i] * Af[k][j] for k in range(m)) for j in range(n)] for i in range(n)]
+    Atb = [sum(Af[k][i] * Fraction(float(b[k])) for k in range(m)) for i in range(n)]
+    return exact.solve(AtA, Atb)
+
+
+@pytest.mark.parametrize("m,n,seed", [(6, 3, 0), (8, 5, 1), (12, 4, 2), (5, 5, 3)])
+def test_gels_aug_matches_exact_normal_equations(orc, m, n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.integers(-9, 10, (m, n)).astype(np.float64)
+    b = rng.integers(-9, 10, m).astype(np.float64)
+    x_ex = _ls_exact(A, b)
+    if any(v.denominator == 0 for v in x_ex):
+        pytest.skip("rank deficient")
+    r = orc.gels_aug(A, b)
+    assert r["info"] == 0
+    x = r["X"][:, 0]
+    sv = np.linalg.svd(A, compute_uv=False)
+    k2 = sv[0] / sv[-1]
+    xm = max(abs(float(v)) for v in x_ex)
+    assert np.max(np.abs(x - np.array([float(v) for v in x_ex]))) <= 100 * k2 ** 2 * U64 * max(xm, 1.0)
+    # the residual is orthogonal to the columns of A (normal equations)
+    R = r["R"][:, 0]
+    assert np.max(np.abs(A.T @ R)) <= 1e3 * U64 * np.max(np.abs(A)) * max(np.max(np.abs(R)), 1.0) * m
+    assert np.allclose(R, b - A @ x, rtol=0, atol=1e-10 * max(np.max(np.abs(b)), 1.0))
+
+
+def test_gels_aug_consistent_system(orc):
+    """b in the range of A: the residual vanishes and x is the generating x."""
+    rng = np.random.default_rng(5)
+    A = rng.integers(-5, 6, (40, 10)).astype(np.float64)
+    xt = rng.integers(-3, 4, 10).astype(np.float64)
+    r = orc.gels_aug(A, A @ xt)
+    assert np.max(np.abs(r["X"][:, 0] - xt)) <= 1e-12
+    assert np.max(np.abs(r["R"])) <= 1e-11
