@@ -143,3 +143,104 @@ def small_integer_matrix(n: int, seed: int = 0, lo: int = -9, hi: int = 9):
     used here) for exact rational pins."""
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.integers(lo, hi + 1, size=(n, n)).astype(np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Sparse systems for the inner-outer iterative method (Algorithm 2,
+# Section 2.2).  The paper's Table 2 matrices come from a public collection
+# that is not available here; these seeded matrices stand in for them with
+# the same orders, nonzeros per row, symmetry and rough condition numbers.
+# Returned as CSR arrays (indptr int32, indices int32 sorted within each row,
+# data FP64), every row holding its diagonal entry.
+# ---------------------------------------------------------------------------
+def _csr_from_coo(n, rows, cols, vals):
+    import scipy.sparse as sp
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()  # duplicates summed
+    A.sort_indices()
+    return (A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
+def sparse_stencil27(g: int, beta: float = 0.3, seed: int = 0):
+    """Convection-diffusion on a g x g x g grid with the 27-point stencil
+    (Dirichlet boundary; n = g^3, 27 entries in interior rows): diagonal 27,
+    neighbour (dx, dy, dz) -(1 + beta (dx + dy + dz) / 3) (1 + 0.1 xi), xi ~
+    U[-1, 1] per entry (nonsymmetric).  The stand-in for Table 2's
+    poisson3Db (3D, nonsymmetric, kappa O(10^3)) at g = 44."""
+    rng = np.random.default_rng(seed)
+    n = g ** 3
+    idx = np.arange(n).reshape(g, g, g)
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [np.full(n, 27.0)]
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                if dx == dy == dz == 0:
+                    continue
+                src = idx[max(0, -dx):g - max(0, dx), max(0, -dy):g - max(0, dy), max(0, -dz):g - max(0, dz)]
+                dst = idx[max(0, dx):g - max(0, -dx), max(0, dy):g - max(0, -dy), max(0, dz):g - max(0, -dz)]
+                rows.append(src.ravel())
+                cols.append(dst.ravel())
+                vals.append(np.full(src.size, -(1.0 + beta * (dx + dy + dz) / 3.0)))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    off = rows != cols
+    vals[off] *= 1.0 + 0.1 * rng.uniform(-1.0, 1.0, size=int(off.sum()))
+    return _csr_from_coo(n, rows, cols, vals)
+
+
+def sparse_random(n: int, nnz_row: int, symmetric: bool = False, dominance: float = 2.0,
+                  indefinite: bool = False, seed: int = 0):
+    """Random sparsity: every row draws nnz_row - 1 off-diagonal columns
+    uniformly (duplicates merged), values N(0,1); symmetric=True draws half as
+    many and mirrors the pattern and values ((R + R^T) / 2).  The diagonal is dominance times the
+    row's off-diagonal absolute sum (so the matrix is nonsingular and its
+    condition number is modest), with a random sign per row if indefinite.
+    Stand-ins for Table 2's cage-11 (nonsymmetric, kappa O(1)) and SiO
+    (symmetric indefinite)."""
+    rng = np.random.default_rng(seed)
+    k = (nnz_row - 1) // 2 if symmetric else nnz_row - 1  # mirroring doubles the off-diagonals
+    rows = np.repeat(np.arange(n), k)
+    cols = rng.integers(0, n - 1, size=n * k)
+    cols = cols + (cols >= rows)  # skip the diagonal
+    vals = rng.standard_normal(n * k)
+    if symmetric:
+        rows, cols = np.concatenate([rows, cols]), np.concatenate([cols, rows])
+        vals = np.concatenate([vals, vals]) * 0.5
+    indptr, indices, data = _csr_from_coo(n, rows, cols, vals)
+    rsum = np.add.reduceat(np.abs(data), indptr[:-1])
+    sign = rng.choice([-1.0, 1.0], size=n) if indefinite else np.ones(n)
+    diag = dominance * np.maximum(rsum, 1.0) * sign
+    rows2 = np.concatenate([np.repeat(np.arange(n), np.diff(indptr)), np.arange(n)])
+    cols2 = np.concatenate([indices, np.arange(n)])
+    return _csr_from_coo(n, rows2, cols2, np.concatenate([data, diag]))
+
+
+# Table 2 stand-ins with the restart values of Table 3 (m_in, m_out) and m of
+# the plain GMRES(m) it is compared with.
+SPARSE_CONFIGS = {
+    "sio_like": dict(kind="random", n=33401, nnz_row=39, symmetric=True, dominance=1.05, indefinite=True,
+                     m_in=30, m_out=20, m=150),
+    "cage11_like": dict(kind="random", n=39082, nnz_row=14, symmetric=False, dominance=2.0, indefinite=False,
+                        m_in=10, m_out=4, m=18),
+    "poisson3db_like": dict(kind="stencil27", g=44, m_in=20, m_out=10, m=50),
+}
+
+
+def sparse_system(name: str, seed: int = 0, scale: float = 1.0):
+    """(indptr, indices, data, b, x_true, cfg) for a Table 2 stand-in;
+    x_true ~ U[-1, 1] and b = A x_true in FP64 (problem construction).
+    scale < 1 shrinks the order (n, or g) for tests."""
+    import scipy.sparse as sp
+    cfg = dict(SPARSE_CONFIGS[name])
+    if cfg["kind"] == "stencil27":
+        g = max(3, int(round(cfg["g"] * scale)))
+        indptr, indices, data = sparse_stencil27(g, seed=seed)
+    else:
+        n = max(8, int(round(cfg["n"] * scale)))
+        indptr, indices, data = sparse_random(n, min(cfg["nnz_row"], n), cfg["symmetric"], cfg["dominance"],
+                                              cfg["indefinite"], seed=seed)
+    n = len(indptr) - 1
+    rng = np.random.default_rng(seed + 7919)
+    x = rng.uniform(-1.0, 1.0, size=n)
+    b = sp.csr_matrix((data, indices, indptr), shape=(n, n)) @ x
+    return indptr, indices, data, b, x, cfg
