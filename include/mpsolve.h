@@ -293,6 +293,78 @@ MP_API int mp_gesv_noalloc(int n, int nrhs, const double *dA, int lda, const dou
                            mp_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Sparse systems: the mixed-precision inner-outer iterative method of
+ * Section 2.2 (Algorithm 2), FGMRES(m_out)-GMRES_SP(m_in).
+ * The matrix is CSR on the DEVICE, owned by the caller: indptr (n + 1 int32,
+ * indptr[0] = 0, non-decreasing, indptr[n] = nnz), indices (nnz int32 column
+ * numbers in [0, n)) and values (nnz FP64).  The library does not check the
+ * structure (it is device data); a malformed one reads out of bounds.
+ * ------------------------------------------------------------------------ */
+
+/* Inner solver of the preconditioner. */
+typedef enum {
+    MP_INNER_FP32 = 0, /* GMRES_SP: one cycle of GMRES(m_in) on the FP32-rounded values, every
+                          operation of the cycle in FP32 (the paper's mixed-precision method) */
+    MP_INNER_FP64 = 1, /* GMRES_DP: the same cycle in FP64 (the paper's FGMRES-GMRES_DP, Fig. 5 left) */
+    MP_INNER_NONE = 2  /* no preconditioner: plain restarted GMRES(m_out) in FP64 (Fig. 5 right) */
+} mp_inner;
+
+typedef struct {
+    int m_out;       /* outer restart: FGMRES steps per cycle, 1..320 (default 20) */
+    int m_in;        /* inner restart: GMRES steps of one preconditioner cycle, 1..320 (default 30) */
+    int inner;       /* mp_inner (default MP_INNER_FP32) */
+    int max_cycles;  /* restarts of the outer method (default 100) */
+    double tol;      /* target normwise backward error ||b - Ax||inf / (||A||inf ||x||inf + ||b||inf)
+                        (default 1e-14) */
+} mp_sparse_opts;
+
+typedef struct {
+    int cycles;       /* outer restart cycles run */
+    int outer_steps;  /* FGMRES steps over all cycles */
+    int inner_steps;  /* GMRES steps of all preconditioner cycles */
+    unsigned flags;   /* MP_FLAG_NOT_CONVERGED (tol not reached in max_cycles), MP_FLAG_TIMEOUT */
+    double bwd_err;   /* backward error of the returned x */
+    int nhist;        /* entries in hist */
+    double hist[32];  /* backward error at the start of each cycle */
+} mp_sparse_stats;
+
+/* Fills *opts with the defaults listed above. */
+MP_API void mp_sparse_default_opts(mp_sparse_opts *opts);
+
+/* Solve A x = b (A n x n sparse, CSR as above; b, x: n FP64 DEVICE vectors)
+ * by Algorithm 2 (Section 2.2) from x_0 = 0: each outer cycle computes
+ * r = b - A x in FP64 and stops when the backward error is <= tol; otherwise
+ * it runs up to m_out flexible-GMRES steps in FP64 whose preconditioner z_k is
+ * one cycle of the inner GMRES for A z = v_k (from z = 0), orthogonalises
+ * A z_k in FP64, ends early once the least-squares residual estimate shows
+ * the accuracy test will pass, and updates x = x + Z y.  Each cycle is one
+ * cooperative launch with bounded grid barriers (a timeout sets
+ * MP_FLAG_TIMEOUT and ends the solve); the call returns after the last cycle.
+ * work: DEVICE scratch of mp_fgmres_workspace_bytes(n, nnz, opts) bytes.
+ * stats may be NULL.  Returns 0, -i for an illegal argument i (1..12 in
+ * order), or a CUDA error (<= -1000). */
+MP_API size_t mp_fgmres_workspace_bytes(int n, long long nnz, const mp_sparse_opts *opts);
+MP_API int mp_fgmres(int n, long long nnz, const int32_t *d_indptr, const int32_t *d_indices,
+                     const double *d_values, const double *d_b, double *d_x, void *work, size_t work_bytes,
+                     const mp_sparse_opts *opts, mp_sparse_stats *stats, void *stream);
+
+/* Steps of Algorithm 2, for testing.  mp_sparse_gmres_cycle: one cycle of
+ * GMRES(m) for A z = v from z = 0 in precision inner (MP_INNER_FP32: values and
+ * v rounded to FP32, every operation in FP32; MP_INNER_FP64), ending early at
+ * breakdown or when its residual estimate is at 4 u of the working precision
+ * times ||v||; z returned in FP64, *steps (host, may be NULL) = steps taken.
+ * work: mp_fgmres_workspace_bytes(n, nnz, opts with m_in = m, m_out = 1).
+ * mp_csr_spmv: y = A x, prec MP_PREC_FP64, or MP_PREC_FP32 (values and x
+ * rounded to FP32, products and sums in FP32, y widened to FP64); x, y: n
+ * FP64 DEVICE vectors.  Both return 0, -i for an illegal argument i, or a CUDA
+ * error (<= -1000). */
+MP_API int mp_sparse_gmres_cycle(int n, long long nnz, const int32_t *d_indptr, const int32_t *d_indices,
+                                 const double *d_values, const double *d_v, double *d_z, int m, int inner,
+                                 void *work, size_t work_bytes, int *steps, void *stream);
+MP_API int mp_csr_spmv(int n, long long nnz, const int32_t *d_indptr, const int32_t *d_indices,
+                       const double *d_values, const double *d_x, double *d_y, int prec, void *stream);
+
+/* ------------------------------------------------------------------------
  * Steps of the hot path, exposed for testing and for callers that keep
  * the factors (Section 3.1.1: SGETRF, SGETRS, DGEMM residual, DAXPY).
  * The low-precision factors live in the caller's workspace as W, an FP32

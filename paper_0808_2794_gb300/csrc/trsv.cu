@@ -74,41 +74,6 @@ base_inverse_kernel(int n, int BI, const T *__restrict__ W, long ldw, T *__restr
         if (c < bs) Uinv[dst + (long)i * BI + c] = x[i][c];
 }
 
-// ---- grid-wide barrier for a cooperative launch (bounded wait: after
-//      limit_ns without the last arrival a CTA records a timeout and returns
-//      false; `expected` arrivals complete a generation, normally the grid)
-__device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, MpDevStatus *st,
-                                             bool *abort_s, unsigned long long limit_ns = 1000000000ULL,
-                                             unsigned expected = 0) {
-    if (expected == 0) expected = gridDim.x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == expected - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd((unsigned *)gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            long long polls = 0;
-            while (*gen == g) {
-                if (++polls > (1LL << 24) || global_ns() - t0 > limit_ns) {
-                    mp_flag(st, MP_FLAG_TIMEOUT);
-                    atomicExch(&st->timeout_site, 2);
-                    *abort_s = true;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return !*abort_s;
-}
-
 // Vector type of 16 bytes.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; };

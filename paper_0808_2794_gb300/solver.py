@@ -50,6 +50,23 @@ class mp_stats(ctypes.Structure):
                     ms_refine=self.ms_refine, ms_fallback=self.ms_fallback)
 
 
+class mp_sparse_opts(ctypes.Structure):
+    _fields_ = [("m_out", ctypes.c_int), ("m_in", ctypes.c_int), ("inner", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class mp_sparse_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer_steps", ctypes.c_int), ("inner_steps", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("bwd_err", ctypes.c_double), ("nhist", ctypes.c_int),
+                ("hist", ctypes.c_double * 32)]
+
+    def as_dict(self):
+        return dict(cycles=self.cycles, outer_steps=self.outer_steps, inner_steps=self.inner_steps,
+                    flags=self.flags, bwd_err=self.bwd_err, hist=list(self.hist[: self.nhist]))
+
+
+INNER = {"fp32": 0, "fp64": 1, "none": 2}
+
 _lib = None
 _lock = threading.Lock()
 
@@ -97,6 +114,13 @@ _SIGS = {
     "mp_gels_workspace_bytes": (_Z, [_I, _I, _I, ctypes.POINTER(mp_opts)]),
     "mp_gels": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, ctypes.c_double, _P, _Z, ctypes.POINTER(mp_opts),
                      ctypes.POINTER(mp_stats), _P]),
+    "mp_sparse_default_opts": (None, [ctypes.POINTER(mp_sparse_opts)]),
+    "mp_fgmres_workspace_bytes": (_Z, [_I, ctypes.c_longlong, ctypes.POINTER(mp_sparse_opts)]),
+    "mp_fgmres": (_I, [_I, ctypes.c_longlong, _P, _P, _P, _P, _P, _P, _Z, ctypes.POINTER(mp_sparse_opts),
+                       ctypes.POINTER(mp_sparse_stats), _P]),
+    "mp_sparse_gmres_cycle": (_I, [_I, ctypes.c_longlong, _P, _P, _P, _P, _P, _I, _I, _P, _Z,
+                                   ctypes.POINTER(ctypes.c_int), _P]),
+    "mp_csr_spmv": (_I, [_I, ctypes.c_longlong, _P, _P, _P, _P, _P, _I, _P]),
     "mp_selftest_workspace_bytes": (_Z, []),
     "mp_selftest_wait_timeout": (_I, [_I, ctypes.c_ulonglong, _P, _Z, ctypes.POINTER(ctypes.c_uint),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
@@ -683,3 +707,79 @@ def gels(A, B, prec="fp32", refine="classical", alpha=0.0, allow_fallback=True, 
     if squeeze:
         return X[:, 0], R[:, 0], d
     return X, R, d
+
+
+# ---------------------------------------------------------------------------
+# Sparse systems: Algorithm 2 (Section 2.2), FGMRES(m_out)-GMRES_SP(m_in)
+# ---------------------------------------------------------------------------
+def sparse_opts(m_out=20, m_in=30, inner="fp32", max_cycles=100, tol=1e-14) -> mp_sparse_opts:
+    o = mp_sparse_opts()
+    load().mp_sparse_default_opts(ctypes.byref(o))
+    o.m_out, o.m_in, o.max_cycles, o.tol = int(m_out), int(m_in), int(max_cycles), float(tol)
+    o.inner = INNER[inner] if isinstance(inner, str) else int(inner)
+    return o
+
+
+def _csr_args(indptr, indices, values):
+    torch = _torch()
+    for t, dt, name in ((indptr, torch.int32, "indptr"), (indices, torch.int32, "indices"),
+                        (values, torch.float64, "values")):
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise MpError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    return indptr.numel() - 1, values.numel()
+
+
+def fgmres(indptr, indices, values, b, m_out=20, m_in=30, inner="fp32", max_cycles=100, tol=1e-14,
+           work=None, stream=None):
+    """Solve A x = b for a CSR matrix (int32 indptr/indices, float64 values,
+    CUDA tensors) by FGMRES(m_out) preconditioned by one cycle of GMRES(m_in)
+    in FP32 (inner="fp32"), FP64 ("fp64") or without a preconditioner
+    ("none": plain restarted GMRES(m_out)).  Returns (x, stats)."""
+    torch = _torch()
+    lib = load()
+    n, nnz = _csr_args(indptr, indices, values)
+    b = b.contiguous()
+    x = torch.empty(n, dtype=torch.float64, device=b.device)
+    o = sparse_opts(m_out, m_in, inner, max_cycles, tol)
+    need = lib.mp_fgmres_workspace_bytes(n, nnz, ctypes.byref(o))
+    if work is None or work.numel() < need:
+        work = workspace(need, b.device)
+    st = mp_sparse_stats()
+    ret = lib.mp_fgmres(n, nnz, indptr.data_ptr(), indices.data_ptr(), values.data_ptr(), b.data_ptr(),
+                        x.data_ptr(), work.data_ptr(), work.numel(), ctypes.byref(o), ctypes.byref(st),
+                        _stream_ptr(stream))
+    _check(ret, "mp_fgmres")
+    return x, st.as_dict()
+
+
+def sparse_gmres_cycle(indptr, indices, values, v, m, inner="fp32", work=None, stream=None):
+    """One cycle of GMRES(m) for A z = v from z = 0 in FP32 or FP64 (the inner
+    solver of Algorithm 2).  Returns (z, steps)."""
+    torch = _torch()
+    lib = load()
+    n, nnz = _csr_args(indptr, indices, values)
+    v = v.contiguous()
+    z = torch.empty(n, dtype=torch.float64, device=v.device)
+    o = sparse_opts(1, m, inner)
+    need = lib.mp_fgmres_workspace_bytes(n, nnz, ctypes.byref(o))
+    if work is None or work.numel() < need:
+        work = workspace(need, v.device)
+    steps = ctypes.c_int(0)
+    ret = lib.mp_sparse_gmres_cycle(n, nnz, indptr.data_ptr(), indices.data_ptr(), values.data_ptr(), v.data_ptr(),
+                                    z.data_ptr(), int(m), INNER[inner], work.data_ptr(), work.numel(),
+                                    ctypes.byref(steps), _stream_ptr(stream))
+    _check(ret, "mp_sparse_gmres_cycle")
+    return z, steps.value
+
+
+def csr_spmv(indptr, indices, values, x, prec="fp64", stream=None):
+    """y = A x for a CSR matrix, in FP64 or FP32 (values and x rounded)."""
+    torch = _torch()
+    lib = load()
+    n, nnz = _csr_args(indptr, indices, values)
+    x = x.contiguous()
+    y = torch.empty(n, dtype=torch.float64, device=x.device)
+    ret = lib.mp_csr_spmv(n, nnz, indptr.data_ptr(), indices.data_ptr(), values.data_ptr(), x.data_ptr(),
+                          y.data_ptr(), PREC[prec], _stream_ptr(stream))
+    _check(ret, "mp_csr_spmv")
+    return y
