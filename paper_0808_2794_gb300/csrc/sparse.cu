@@ -46,6 +46,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxM = 320;      // largest m_in / m_out (Table 3 goes up to 300)
 constexpr int kMaxGrid = 1024;  // largest cooperative grid (sizes the partial sums)
+constexpr int kStageBytes = 160 * 1024;  // staged x: 40960 FP32 or 20480 FP64 columns per CTA
+constexpr int kRsmBytes = 16 * 1024;     // an R in shared memory: m <= 44 (FP64) or 63 (FP32)
 
 enum Mode { kCycle = 0, kInnerOnly = 1 };
 
@@ -67,6 +69,7 @@ struct SpCtrl {
 struct SpArgs {
     int n, mode, m_in, m_out, inner;  // inner: 0 FP32, 1 FP64, 2 none (plain restarted GMRES)
     long ld;              // stride of the basis vectors (n rounded up to 32)
+    int stage_bytes;      // dynamic shared memory for the staged x
     const int *indptr, *indices;
     const double *val64;
     const void *valin;    // values in the inner precision (val64 itself for FP64)
@@ -189,26 +192,128 @@ __device__ void cta_update(T *w, const T *V, long ldv, int k, const T *h, int r0
     }
 }
 
+// Columns [c0, c1) of x into shared memory xs (xs[c - c0a], c0a = c0 rounded
+// down to a 16-byte piece), coalesced, past L1 (other CTAs wrote x in this
+// launch): 16-byte pieces while they lie below c1, elements after.
+template <typename T>
+__device__ void stage_x(const T *x, int c0, int c1, T *xs) {
+    using VT = typename Vec<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const int c0a = c0 / VW * VW;
+    const int vb = c1 / VW * VW > c0a ? c1 / VW * VW : c0a;
+    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    if (vec) {
+        for (int q = threadIdx.x; q < (vb - c0a) / VW; q += kThreads)
+            reinterpret_cast<VT *>(xs)[q] = __ldcg(reinterpret_cast<const VT *>(x + c0a) + q);
+        for (int c = vb + threadIdx.x; c < c1; c += kThreads) xs[c - c0a] = __ldcg(x + c);
+    } else {
+        for (int c = c0a + threadIdx.x; c < c1; c += kThreads) xs[c - c0a] = __ldcg(x + c);
+    }
+    __syncthreads();
+}
+
+// Products of one row's entries e0 + sub, e0 + sub + L, ... below e1 with x
+// (staged in xs when set, else from global memory past L1), two in flight.
+template <typename T, typename TV, int L>
+__device__ __forceinline__ T row_dot(const int *__restrict__ indices, const TV *__restrict__ val, const T *x,
+                                     const T *xs, int xoff, int e0, int e1) {
+    T s0 = T(0), s1 = T(0);
+    int e = e0;
+    if (xs) {
+        for (; e + L < e1; e += 2 * L) {
+            s0 = fma((T)val[e], xs[indices[e] - xoff], s0);
+            s1 = fma((T)val[e + L], xs[indices[e + L] - xoff], s1);
+        }
+        if (e < e1) s0 = fma((T)val[e], xs[indices[e] - xoff], s0);
+    } else {
+        for (; e + L < e1; e += 2 * L) {
+            s0 = fma((T)val[e], __ldcg(x + indices[e]), s0);
+            s1 = fma((T)val[e + L], __ldcg(x + indices[e + L]), s1);
+        }
+        if (e < e1) s0 = fma((T)val[e], __ldcg(x + indices[e]), s0);
+    }
+    return s0 + s1;
+}
+
 // y[row] = scale * sum_l a_l x[col_l] for the rows [r0, r1), L lanes per row,
 // in precision T (values converted from TV, i.e. rounded when TV is wider);
-// with b, y[row] = b[row] - sum (the residual).  x is read past L1: other
-// CTAs wrote it in this launch.
+// with b, y[row] = b[row] - sum (the residual).  A lane group takes two rows
+// per pass (their loads in flight together) and fetches the next pass's row
+// pointers while it works.
 template <typename T, typename TV, int L>
 __device__ void spmv_rows(const int *__restrict__ indptr, const int *__restrict__ indices, const TV *__restrict__ val,
-                          const T *x, T *y, int r0, int r1, T scale, const double *__restrict__ b) {
+                          const T *x, const T *xs, int xoff, T *y, int r0, int r1, T scale,
+                          const double *__restrict__ b) {
     const int sub = threadIdx.x % L, grp = threadIdx.x / L;
     constexpr int GROUPS = kThreads / L;
-    for (int row0 = r0; row0 < r1; row0 += GROUPS) {
-        const int row = row0 + grp;
-        T s = T(0);
-        if (row < r1) {
-            const int e1 = indptr[row + 1];
-            for (int e = indptr[row] + sub; e < e1; e += L) s = fma((T)val[e], __ldcg(x + indices[e]), s);
+    int ra = r0 + grp, rb = ra + GROUPS;
+    int pa0 = ra < r1 ? indptr[ra] : 0, pa1 = ra < r1 ? indptr[ra + 1] : 0;
+    int pb0 = rb < r1 ? indptr[rb] : 0, pb1 = rb < r1 ? indptr[rb + 1] : 0;
+    for (int row0 = r0; row0 < r1; row0 += 2 * GROUPS) {
+        // the next pass's row pointers
+        const int na = ra + 2 * GROUPS, nb = rb + 2 * GROUPS;
+        const int qa0 = na < r1 ? indptr[na] : 0, qa1 = na < r1 ? indptr[na + 1] : 0;
+        const int qb0 = nb < r1 ? indptr[nb] : 0, qb1 = nb < r1 ? indptr[nb + 1] : 0;
+        T sa = row_dot<T, TV, L>(indices, val, x, xs, xoff, pa0 + sub, pa1);
+        T sb = row_dot<T, TV, L>(indices, val, x, xs, xoff, pb0 + sub, pb1);
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, off);
+            sb += __shfl_xor_sync(0xffffffffu, sb, off);
+        }
+        if (sub == 0) {
+            if (ra < r1) y[ra] = b ? (T)(b[ra] - (double)sa) : sa * scale;
+            if (rb < r1) y[rb] = b ? (T)(b[rb] - (double)sb) : sb * scale;
+        }
+        ra = na;
+        rb = nb;
+        pa0 = qa0;
+        pa1 = qa1;
+        pb0 = qb0;
+        pb1 = qb1;
+    }
+}
+
+// The columns this CTA's rows reference, and whether x restricted to them
+// fits the staging area: the sparse products then gather from shared memory.
+struct ColSpan {
+    int c0, c1, xoff;
+    bool fits32, fits64;
+};
+__device__ ColSpan col_span(const int *indptr, const int *indices, int r0, int r1, int stage_bytes, int *red) {
+    int lo = INT_MAX, hi = -1;
+    if (r1 > r0)
+        for (int e = indptr[r0] + threadIdx.x; e < indptr[r1]; e += kThreads) {
+            const int c = indices[e];
+            lo = min(lo, c);
+            hi = max(hi, c);
         }
 #pragma unroll
-        for (int off = L / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (row < r1 && sub == 0) y[row] = b ? (T)(b[row] - (double)s) : s * scale;
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
     }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = lo;
+        red[kWarps + (threadIdx.x >> 5)] = hi;
+    }
+    __syncthreads();
+    ColSpan cs;
+    lo = INT_MAX;
+    hi = -1;
+    for (int w = 0; w < kWarps; ++w) {
+        lo = min(lo, red[w]);
+        hi = max(hi, red[kWarps + w]);
+    }
+    __syncthreads();
+    if (hi < lo) lo = hi = 0;  // no entries
+    cs.c0 = lo;
+    cs.c1 = hi + 1;
+    cs.xoff = lo / 4 * 4;  // the FP32 staging's rounding (FP64 rounds to 2: recomputed there)
+    const long span = (long)cs.c1 - lo / 4 * 4 + 4;
+    cs.fits32 = span * 4 <= stage_bytes;
+    cs.fits64 = span * 8 <= stage_bytes;
+    return cs;
 }
 
 // Givens rotation (c, s) with c a + s b = hypot(a, b) and -s a + c b = 0.
@@ -286,15 +391,16 @@ __device__ bool cgs2(const SpArgs &a, T *wn, const T *V, int k, int r0, int r1, 
 // Returns false if a grid barrier timed out.
 template <typename T, int L>
 __device__ bool inner_cycle(const SpArgs &a, const double *v, double *zdst, int r0, int r1, int &phase,
-                            bool &abort_s, T *h1, T *h2, int *steps_out, T *beta_out) {
+                            bool &abort_s, T *h1, T *h2, int *steps_out, T *beta_out, const ColSpan &span,
+                            T *xstage, T *R, T *g, T *cs, T *sn) {
+    const bool stage_in = sizeof(T) == 4 ? span.fits32 : span.fits64;
     const int m = a.m_in, tid = threadIdx.x, ps = a.pstride;
     const long ld = a.ld;
     const bool lead = blockIdx.x == 0 && tid == 0;
     T *Vin = reinterpret_cast<T *>(a.Vin);
     T *Win = reinterpret_cast<T *>(a.Win);
     const T *val = reinterpret_cast<const T *>(a.valin);
-    T *R = reinterpret_cast<T *>(a.Rin), *g = reinterpret_cast<T *>(a.gin);
-    T *cs = reinterpret_cast<T *>(a.csin), *sn = reinterpret_cast<T *>(a.snin), *y = reinterpret_cast<T *>(a.yin);
+    T *y = reinterpret_cast<T *>(a.yin);
     // r0 = fl_T(v), unnormalised, into Win[0], and its norm
     for (int row = r0 + tid; row < r1; row += kThreads) Win[row] = (T)v[row];
     __syncthreads();
@@ -315,7 +421,14 @@ __device__ bool inner_cycle(const SpArgs &a, const double *v, double *zdst, int 
             T *vj = Vin + j * ld;
             const T inv = T(1) / hprev;
             for (int row = r0 + tid; row < r1; row += kThreads) vj[row] = wp[row] * inv;
-            spmv_rows<T, T, L>(a.indptr, a.indices, val, wp, wn, r0, r1, inv, nullptr);
+            const T *xs = nullptr;
+            int xoff = 0;
+            if (stage_in) {
+                stage_x<T>(wp, span.c0, span.c1, xstage);
+                xs = xstage;
+                xoff = span.c0 / (16 / (int)sizeof(T)) * (16 / (int)sizeof(T));
+            }
+            spmv_rows<T, T, L>(a.indptr, a.indices, val, wp, xs, xoff, wn, r0, r1, inv, nullptr);
             __syncthreads();
             T hnext;
             if (!cgs2<T>(a, wn, Vin, j + 1, r0, r1, phase, abort_s, h1, h2, hnext)) return false;
@@ -354,7 +467,12 @@ template <typename Tin, int L>
 __global__ void __launch_bounds__(kThreads) fgmres_kernel(const SpArgs a) {
     __shared__ double hd1[kMaxM + 2], hd2[kMaxM + 2];
     __shared__ Tin hi1[kMaxM + 2], hi2[kMaxM + 2];
+    // the small problems' rotations and right-hand sides (CTA 0 uses them)
+    __shared__ double gout_s[kMaxM + 2], csout_s[kMaxM + 2], snout_s[kMaxM + 2];
+    __shared__ Tin gin_s[kMaxM + 2], csin_s[kMaxM + 2], snin_s[kMaxM + 2];
+    __shared__ int red[2 * kWarps];
     __shared__ bool abort_s;
+    extern __shared__ __align__(16) unsigned char dyn[];  // staged x, then the two R when they fit
     if (threadIdx.x == 0) abort_s = false;
     __syncthreads();
     const int n = a.n, tid = threadIdx.x, ps = a.pstride;
@@ -363,17 +481,30 @@ __global__ void __launch_bounds__(kThreads) fgmres_kernel(const SpArgs a) {
     // row blocks start at multiples of 32 (16-byte pieces of every vector)
     const int per = ((n + (int)gridDim.x - 1) / (int)gridDim.x + 31) / 32 * 32;
     const int r0 = min(n, (int)blockIdx.x * per), r1 = min(n, r0 + per);
+    const ColSpan span = col_span(a.indptr, a.indices, r0, r1, a.stage_bytes, red);
+    Tin *xs_in = reinterpret_cast<Tin *>(dyn);
+    double *xs64 = reinterpret_cast<double *>(dyn);
+    // R of the small problems in shared memory when it fits (else global)
+    const size_t rin_bytes = sizeof(Tin) * (size_t)(a.m_in + 1) * a.m_in;
+    const size_t rout_bytes = sizeof(double) * (size_t)(a.m_out + 1) * a.m_out;
+    double *Rout = rout_bytes <= kRsmBytes ? reinterpret_cast<double *>(dyn + a.stage_bytes) : a.Rout;
+    Tin *Rin = rin_bytes <= kRsmBytes ? reinterpret_cast<Tin *>(dyn + a.stage_bytes + kRsmBytes)
+                                      : reinterpret_cast<Tin *>(a.Rin);
     int phase = 0;
     if (a.mode == kInnerOnly) {
         int steps = 0;
         Tin beta = Tin(0);
-        if (!inner_cycle<Tin, L>(a, a.rhs_inner, a.z_inner, r0, r1, phase, abort_s, hi1, hi2, &steps, &beta)) return;
+        if (!inner_cycle<Tin, L>(a, a.rhs_inner, a.z_inner, r0, r1, phase, abort_s, hi1, hi2, &steps, &beta, span,
+                                 xs_in, Rin, gin_s, csin_s, snin_s))
+            return;
         if (lead) a.ctrl->inner_steps = steps;
         return;
     }
     // ---- r = b - A x (FP64), the accuracy test
     double *r = a.W64, *w64 = a.W64 + ld;
-    spmv_rows<double, double, L>(a.indptr, a.indices, a.val64, a.x, r, r0, r1, 1.0, a.b);
+    if (span.fits64) stage_x<double>(a.x, span.c0, span.c1, xs64);
+    spmv_rows<double, double, L>(a.indptr, a.indices, a.val64, a.x, span.fits64 ? xs64 : nullptr, span.c0 / 2 * 2, r,
+                                 r0, r1, 1.0, a.b);
     __syncthreads();
     {
         double rm = 0.0, xm = 0.0;
@@ -409,7 +540,7 @@ __global__ void __launch_bounds__(kThreads) fgmres_kernel(const SpArgs a) {
     const double xs = anorm > 0.0 ? fmax(xmax, bnorm / anorm) : xmax;
     const double tau = 0.5 * a.tol * (anorm * xs + bnorm);
     for (int row = r0 + tid; row < r1; row += kThreads) a.Vout[row] = r[row] / beta;
-    if (lead) a.gout[0] = beta;
+    if (lead) gout_s[0] = beta;
     int used = 0, inner_total = 0;
     for (int k = 0; k < a.m_out; ++k) {
         double *zk = a.Zout + k * ld;
@@ -419,20 +550,23 @@ __global__ void __launch_bounds__(kThreads) fgmres_kernel(const SpArgs a) {
         } else {
             int steps = 0;
             Tin bi = Tin(0);
-            if (!inner_cycle<Tin, L>(a, vk, zk, r0, r1, phase, abort_s, hi1, hi2, &steps, &bi)) return;
+            if (!inner_cycle<Tin, L>(a, vk, zk, r0, r1, phase, abort_s, hi1, hi2, &steps, &bi, span, xs_in, Rin,
+                                     gin_s, csin_s, snin_s))
+                return;
             inner_total += steps;
         }
         __syncthreads();
         if (!grid_barrier(a.bar, a.bar + 1, a.st, &abort_s)) return;  // z_k complete on every row
-        spmv_rows<double, double, L>(a.indptr, a.indices, a.val64, zk, w64, r0, r1, 1.0, nullptr);
+        if (span.fits64) stage_x<double>(zk, span.c0, span.c1, xs64);
+        spmv_rows<double, double, L>(a.indptr, a.indices, a.val64, zk, span.fits64 ? xs64 : nullptr, span.c0 / 2 * 2,
+                                     w64, r0, r1, 1.0, nullptr);
         __syncthreads();
         double hnext;
         if (!cgs2<double>(a, w64, a.Vout, k + 1, r0, r1, phase, abort_s, hd1, hd2, hnext)) return;
         if (lead) {
-            const double est = givens_step<double>(a.Rout, a.gout, a.csout, a.snout, hd1, hd2, hnext, k,
-                                                   a.m_out + 1);
+            const double est = givens_step<double>(Rout, gout_s, csout_s, snout_s, hd1, hd2, hnext, k, a.m_out + 1);
             const bool stop = hnext == 0.0 || est <= tau || k + 1 == a.m_out;
-            if (stop) back_solve<double>(a.Rout, a.gout, a.yout, k + 1, a.m_out + 1);
+            if (stop) back_solve<double>(Rout, gout_s, a.yout, k + 1, a.m_out + 1);
             a.ctrl->stop = stop ? 1 : 0;
             a.ctrl->est = est;
         }
@@ -557,18 +691,22 @@ SpLayout sp_layout(int n_, long nnz, int m_in, int m_out, int inner) {
 template <typename Tin, int L>
 cudaError_t launch_fgmres_t(const SpArgs &a, cudaStream_t s) {
     auto kern = fgmres_kernel<Tin, L>;
+    const size_t smem = (size_t)kStageBytes + 2 * (size_t)kRsmBytes;
+    cudaError_t e = mp_smem_attr(kern, smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // one CTA per SM: the grid barrier's cost grows with the CTA count, and
-    // 256 threads per SM already keep the L2-resident product busy
+    // one CTA per SM: the grid barrier's cost grows with the CTA count
     int grid = std::min(sm_count(), kMaxGrid);
     grid = std::max(1, std::min(grid, (a.n + 31) / 32));
     SpArgs args = a;
+    args.stage_bytes = kStageBytes;
     void *kargs[] = {(void *)&args};
     mp_note_launch();
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kThreads), kargs, 0, s);
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kThreads), kargs, smem,
+                                       s);
 }
 
 cudaError_t launch_fgmres(const SpArgs &a, int lanes, cudaStream_t s) {
