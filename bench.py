@@ -7,8 +7,8 @@ step = one whole mixed-precision solve through the C ABI (mp_gesv): FP64->FP32
 conversion, low-precision LU with partial pivoting (default rung fp16x3: the
 trailing updates as three fp16 tensor-core products, about FP32 accurate),
 FP64 iterative refinement to a normwise backward error <= 1e-14 (and the FP64
-fallback, if taken).  --workload chol|batched|adjoint times the secondary
-workloads instead (one JSON line each, not the headline).
+fallback, if taken).  --workload chol|batched|adjoint|fig4|dd|sparse times the
+secondary workloads instead (one JSON line each, not the headline).
 
   value      = (2 n^3 / 3) * N_ranks / (max-over-ranks time per step), GFLOP/s,
                inputs resident in HBM (A is 2.1 GB, larger than L2).
@@ -641,6 +641,85 @@ def run_dd(args):
     return 0
 
 
+def run_sparse(args):
+    """Algorithm 2 (Section 2.2) on the GPU, the paper's Fig. 5 comparison:
+    for each seeded stand-in of a Table 2 matrix (same order, nonzeros per
+    row, symmetry and rough condition number; the restart values of Table 3),
+    the solve time of FGMRES(m_out)-GMRES_SP(m_in) (inner cycle in FP32), of
+    FGMRES-GMRES_DP (inner cycle in FP64, Fig. 5 left) and of plain restarted
+    GMRES(m) in FP64 (Fig. 5 right), each to a backward error of 1e-14 from
+    x_0 = 0 (median of the timed steps, L2 flushed between steps), with the
+    outer and inner step counts; the CPU oracle's FGMRES-GMRES_SP (numpy, FP32
+    inner) on the same system is timed once beside it.  The roofline entry
+    counts the method's algorithmic bytes (stored entries and basis vectors
+    read and written) over the solve time against the HBM copy bandwidth;
+    the matrices and bases stay in L2 and the cycle is bound by grid-barrier
+    latency, so the fraction is low by construction.  One JSON line."""
+    import torch
+    from paper_0808_2794_gb300 import inputs, solver
+    import oracle.fgmres as ofg
+    torch.cuda.set_device(0)
+    peaks = load_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    t_all = time.perf_counter()
+    for name, cfg in inputs.SPARSE_CONFIGS.items():
+        ip, ix, d, b, xt, _ = inputs.sparse_system(name, seed=0)
+        n, nnz = len(ip) - 1, len(d)
+        dev = [torch.from_numpy(a).cuda() for a in (ip, ix, d)]
+        db = torch.from_numpy(b).cuda()
+        row = {"matrix": name, "n": n, "nnz": nnz, "symmetric": bool(cfg.get("symmetric", False)),
+               "m_in": cfg["m_in"], "m_out": cfg["m_out"], "m": cfg["m"]}
+        for label, inner, mo in (("fgmres_gmres_sp", "fp32", cfg["m_out"]), ("fgmres_gmres_dp", "fp64", cfg["m_out"]),
+                                 ("gmres_dp", "none", cfg["m"])):
+            work = None
+            for _ in range(max(1, args.warmup)):
+                x, st = solver.fgmres(*dev, db, m_out=mo, m_in=cfg["m_in"], inner=inner)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                x, st = solver.fgmres(*dev, db, m_out=mo, m_in=cfg["m_in"], inner=inner)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            xh = x.cpu().numpy()
+            fwd = float(np.max(np.abs(xh - xt)) / np.max(np.abs(xt)))
+            row[label] = {"ms": float(np.median(ts)), "cycles": st["cycles"], "outer_steps": st["outer_steps"],
+                          "inner_steps": st["inner_steps"], "flags": st["flags"], "bwd_err": st["bwd_err"],
+                          "fwd_err_vs_xtrue": fwd}
+        sp = row["fgmres_gmres_sp"]
+        # algorithmic bytes: FP32 entries (value + index) and vectors per inner
+        # step, FP64 per outer step; CGS2 reads the basis twice and updates twice
+        m_in, so = cfg["m_in"], sp["outer_steps"]
+        inner_b = so * sum(8.0 * nnz + 4.0 * n * (2 + 4 * (j + 1)) for j in range(m_in))
+        outer_b = sum(12.0 * nnz + 8.0 * n * (2 + 4 * (k + 1)) for k in range(so))
+        row["algorithmic_bytes"] = inner_b + outer_b
+        row["speedup_vs_fgmres_dp"] = row["fgmres_gmres_dp"]["ms"] / sp["ms"]
+        row["speedup_vs_gmres_dp"] = row["gmres_dp"]["ms"] / sp["ms"]
+        t0 = time.perf_counter()
+        ref = ofg.fgmres(ip, ix, d, b, cfg["m_out"], cfg["m_in"], inner=np.float32)
+        row["cpu_oracle"] = {"ms": (time.perf_counter() - t0) * 1e3, "outer_steps": ref["outer_steps"],
+                             "converged": ref["converged"], "cores": 1,
+                             "kind": "oracle (numpy, FGMRES-GMRES_SP, FP32 inner)"}
+        rows.append(row)
+    big = max(rows, key=lambda r: r["n"])
+    achieved = big["algorithmic_bytes"] / (big["fgmres_gmres_sp"]["ms"] * 1e-3) / 1e9
+    line = {"metric": "Algorithm 2: FGMRES-GMRES_SP solve time to bwd err <= 1e-14 (ms), Table 2 stand-ins, 1 GB300",
+            "unit": "ms", "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "seeded stand-ins of Table 2 matrices (SiO, cage-11, poisson3Db shapes), "
+                                   "restarts from Table 3, x_true ~ U[-1,1], b = A x_true",
+                       "l2": "256 MB written between timed steps"},
+            "roofline": {"bound": "hbm", "kernel": "fgmres_kernel<float>", "matrix": big["matrix"],
+                         "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                         "peak_source": peaks["_source"]},
+            "table": rows, "seconds": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -652,7 +731,7 @@ def main():
     ap.add_argument("--prec", default="fp16x3")
     ap.add_argument("--refine", default="classical", choices=["classical", "gmres", "auto"])
     ap.add_argument("--fig4-count", type=int, default=200)
-    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint", "fig4", "dd"],
+    ap.add_argument("--workload", default="lu", choices=["lu", "chol", "batched", "adjoint", "fig4", "dd", "sparse"],
                     help="lu: the headline dense solve; the others time the secondary "
                          "workloads (SPD Cholesky, batched small systems, adjoint solve)")
     ap.add_argument("--kappa", type=float, default=1e4, help="condition number for --workload chol")
@@ -670,6 +749,8 @@ def main():
         return run_fig4(args)
     if args.workload == "dd":
         return run_dd(args)
+    if args.workload == "sparse":
+        return run_sparse(args)
     if args.workload != "lu":
         return run_secondary(args)
 
