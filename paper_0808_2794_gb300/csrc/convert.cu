@@ -3,7 +3,7 @@
 // LU factorization ... the original A is kept"; DLANGE in Table 7).
 //
 // A (FP64, column-major, the caller's) is read once, coalesced, through a
-// 32x32 shared-memory transpose into the row-major W; row sums of |a_ij| are
+// 64x64 shared-memory transpose into the row-major W; row sums of |a_ij| are
 // accumulated for ||A||_inf, and any NaN/Inf raises MP_FLAG_NONFINITE_INPUT.
 // Conversion to FP32 is round-to-nearest-even (__double2float_rn).
 #include "common.cuh"
@@ -12,59 +12,87 @@
 namespace {
 
 constexpr int kTile = 32;
-constexpr int kColTiles = 8;  // each CTA walks 8 column tiles: fewer row-sum atomics
+constexpr int kColTiles = 4;  // each CTA walks 4 column tiles: fewer row-sum atomics
 
 template <typename Tout>
 __device__ __forceinline__ Tout cvt(double v);
 template <> __device__ __forceinline__ float cvt<float>(double v) { return __double2float_rn(v); }
 template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
 
+// 64 x 64 tiles: a warp reads 64 rows of a column as 16-byte pieces (512
+// contiguous bytes per instruction), eight columns in flight per thread; after
+// the transpose in shared memory a warp writes 64 values of a row (256 bytes
+// of FP32) per instruction.  Long contiguous runs on both sides keep DRAM
+// pages open; a CTA walks kColTiles column tiles to amortise the row-sum
+// atomics.
+constexpr int kT = 64;
+
 template <typename Tout>
 __global__ void __launch_bounds__(256)
 convert_transpose_kernel(int n, const double *__restrict__ A, long lda, Tout *__restrict__ W,
                          long ldw, double *__restrict__ rowsum, MpDevStatus *st) {
-    // 32 rows x 64 columns per step: 8 independent loads per thread in flight
-    __shared__ Tout tile[2 * kTile][kTile + 1];  // [column][row]
-    __shared__ double rs[8][kTile];
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int r0 = blockIdx.x * kTile;
-    double rsum = 0.0;
+    __shared__ Tout tile[kT][kT + 1];  // [column][row]
+    __shared__ double rs[8][kT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * kT;
+    const int ra = r0 + 2 * lane;  // this lane's two rows
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) | (uintptr_t)(lda * 8)) & 15) == 0;
+    double rsum0 = 0.0, rsum1 = 0.0;
     bool bad = false;
-    for (int ct = 0; ct < kColTiles; ct += 2) {
-        const int c0 = (blockIdx.y * kColTiles + ct) * kTile;
+    for (int ct = 0; ct < kColTiles; ++ct) {
+        const int c0 = (blockIdx.y * kColTiles + ct) * kT;
         if (c0 >= n) break;
-        double v[8];
+        double2 v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int c = c0 + ty + 8 * q, r = r0 + tx;
-            v[q] = (r < n && c < n) ? __ldcs(A + (long)c * lda + r) : 0.0;
+            const int c = c0 + warp + 8 * q;
+            const double *src = A + (long)c * lda + ra;
+            if (c < n && vec && ra + 1 < n) {
+                v[q] = __ldcs(reinterpret_cast<const double2 *>(src));
+            } else {
+                v[q].x = (c < n && ra < n) ? __ldcs(src) : 0.0;
+                v[q].y = (c < n && ra + 1 < n) ? __ldcs(src + 1) : 0.0;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            if (!(fabs(v[q]) <= 1.79769313486231570815e308)) bad = true;
-            rsum += fabs(v[q]);
-            tile[ty + 8 * q][tx] = cvt<Tout>(v[q]);
+            if (!(fabs(v[q].x) <= 1.79769313486231570815e308) || !(fabs(v[q].y) <= 1.79769313486231570815e308))
+                bad = true;
+            rsum0 += fabs(v[q].x);
+            rsum1 += fabs(v[q].y);
+            tile[warp + 8 * q][2 * lane] = cvt<Tout>(v[q].x);
+            tile[warp + 8 * q][2 * lane + 1] = cvt<Tout>(v[q].y);
         }
         __syncthreads();
+        // rows r0 + warp + 8 q, columns c0 + 2 lane, c0 + 2 lane + 1
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = r0 + ty + 8 * q;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + tx + 32 * h;
-                if (r < n && c < n) W[(long)r * ldw + c] = tile[tx + 32 * h][ty + 8 * q];
+        for (int q = 0; q < 8; ++q) {
+            const int r = r0 + warp + 8 * q, c = c0 + 2 * lane;
+            if (r < n) {
+                Tout *dst = W + (long)r * ldw + c;
+                const Tout x0 = tile[2 * lane][warp + 8 * q], x1 = tile[2 * lane + 1][warp + 8 * q];
+                if (sizeof(Tout) == 4 && c + 1 < n && ((reinterpret_cast<uintptr_t>(dst) & 7) == 0)) {
+                    float2 pr;
+                    pr.x = (float)x0;
+                    pr.y = (float)x1;
+                    *reinterpret_cast<float2 *>(dst) = pr;
+                } else {
+                    if (c < n) dst[0] = x0;
+                    if (c + 1 < n) dst[1] = x1;
+                }
             }
         }
         __syncthreads();
     }
     if (bad) mp_flag(st, MP_FLAG_NONFINITE_INPUT);
-    rs[ty][tx] = rsum;
+    rs[warp][2 * lane] = rsum0;
+    rs[warp][2 * lane + 1] = rsum1;
     __syncthreads();
-    if (ty == 0) {
+    if (threadIdx.x < kT) {
         double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += rs[q][tx];
-        if (r0 + tx < n) atomicAdd(&rowsum[r0 + tx], t);
+        for (int w = 0; w < 8; ++w) t += rs[w][threadIdx.x];
+        if (r0 + threadIdx.x < n) atomicAdd(&rowsum[r0 + threadIdx.x], t);
     }
 }
 
@@ -139,10 +167,9 @@ template <typename Tout>
 cudaError_t launch_convert_transpose(int n, const double *A, long lda, Tout *W, long ldw,
                                      double *rowsum, MpDevStatus *st, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    dim3 block(32, 8);
-    dim3 grid((n + kTile - 1) / kTile, (n + kTile * kColTiles - 1) / (kTile * kColTiles));
+    dim3 grid((n + kT - 1) / kT, (n + kT * kColTiles - 1) / (kT * kColTiles));
     mp_note_launch();
-    convert_transpose_kernel<Tout><<<grid, block, 0, s>>>(n, A, lda, W, ldw, rowsum, st);
+    convert_transpose_kernel<Tout><<<grid, 256, 0, s>>>(n, A, lda, W, ldw, rowsum, st);
     return cudaGetLastError();
 }
 template cudaError_t launch_convert_transpose<float>(int, const double *, long, float *, long,

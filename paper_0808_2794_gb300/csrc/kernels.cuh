@@ -145,6 +145,7 @@ cudaError_t launch_transpose(int n, const T *W, long ldw, T *Wt, long ldwt, cuda
 template <typename T> int trsv_inverse_block(int n);
 template <typename T> size_t trsv_inverse_bytes(int n);  // per triangle
 template <typename T> size_t trsv_tmp_bytes(int n);
+template <typename T> size_t trsv_sync_bytes(int n);  // counters of one solve (zeroed by the launch)
 template <typename T>
 cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
                                   bool lower_unit = true, bool upper_unit = false);

@@ -242,7 +242,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.Uinv = carve(off, inv_bytes);
     L.invtmp = carve(off, std::max(trsv_tmp_bytes<float>(n), fp64_space ? trsv_tmp_bytes<double>(n) : 0));
     L.acc = carve(off, el * (size_t)n * rhs);
-    L.bar = carve(off, sizeof(unsigned) * 4);
+    L.bar = carve(off, std::max(trsv_sync_bytes<float>(n), fp64_space ? trsv_sync_bytes<double>(n) : 0));
     L.R = carve(off, sizeof(double) * (size_t)n * rhs);
     L.Y = carve(off, el * (size_t)n * rhs);
     L.Z = carve(off, el * (size_t)n * rhs);
@@ -1411,7 +1411,7 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     L.Uinv = carve(off, trsv_inverse_bytes<float>(n));
     L.invtmp = carve(off, trsv_tmp_bytes<float>(n));
     L.acc = carve(off, sizeof(float) * (size_t)n * rhs);
-    L.bar = carve(off, sizeof(unsigned) * 4);
+    L.bar = carve(off, trsv_sync_bytes<float>(n));
     L.Y = carve(off, sizeof(float) * (size_t)n * rhs);
     L.Z = carve(off, sizeof(float) * (size_t)n * rhs);
     L.part = carve(off, sizeof(double) * (size_t)L.ksplit * n * rhs);

@@ -7,15 +7,12 @@
 // rows in FP32 for n >= 2048): 128-row (64 in FP64) blocks are inverted by
 // substitution, then neighbours are merged level by level with batched
 // GEMMs (X21 = -X22 L21 X11 for L, X12 = -X11 U12 X22 for U).  A solve is
-// then only n/BI dependent steps of one persistent cooperative kernel:
-//   A. y_b = inv(D_b) acc_b           (a BI x BI matrix-vector product)
-//   -- grid barrier --
-//   B. acc_r -= W[r, block b] y_b for every row r still to be solved
-//      (streams the block column of the factor once, coalesced rows)
-//   -- grid barrier --
-// so the dependency chain is n/BI long instead of n, and every step streams
-// its part of the factor with all SMs.  Grid barriers are bounded and report
-// MP_FLAG_TIMEOUT instead of hanging.
+// then n/BI dependent steps, each y_b = inv(D_b) acc_b (a BI x BI product)
+// followed by acc_r -= W[r, block b] y_b for the rows still to be solved.
+// One persistent cooperative kernel runs them as a dataflow: a small group of
+// CTAs follows the chain (the product with the inverse, then the next block's
+// rows), the rest stream the remaining block columns from a work queue, and
+// counters with bounded waits (MP_FLAG_TIMEOUT instead of a hang) order them.
 //
 // The right-hand side r (FP64) is scaled by s = 2^ceil(log2 ||r||inf) before
 // it is rounded to the working precision (exact power-of-two scaling keeps
@@ -126,23 +123,119 @@ __device__ __forceinline__ void row_dot(const T *__restrict__ src, int bs, const
     }
 }
 
+// ---- the dataflow solve ----------------------------------------------------
+// Blocks of BI rows are solved in order (first to last for L, last to first
+// for U); a block's rows are split into chunks of RC rows.  Work items:
+//   A(s)       y_b = inv(D_b) acc_b for block b = block(s), chunk by chunk
+//   near(s)    acc_c -= W[c rows, block b] y_b for c = block(s + 1)
+//   far(s, t)  the same for c = block(t), t >= s + 2
+// A small group of "critical" CTAs runs A and near for every step in turn
+// (the dependency chain); the other CTAs take the far items from a queue in
+// the order (s, t, chunk) and stream the bulk of the factor meanwhile.  Each
+// chunk's updates are applied in step order (a per-chunk counter), so every
+// row sees the same sequence of subtractions as a step-by-step solve and the
+// result does not depend on the schedule.  Counters (device memory, zeroed
+// before the launch):
+//   ycnt[b]   chunks of y_b written        updcnt[b]  chunk updates applied to block b
+//   chunk[b][j] updates applied to chunk j of block b (release/acquire)
+// Waits are bounded: after about a second a CTA records MP_FLAG_TIMEOUT,
+// raises the abort word and returns; every wait also gives up on abort.
+constexpr int kRC = 8;   // rows per chunk: the chain's items are 8 rows x BI of the factor (32 KB in FP32)
+constexpr int kFG = 2;   // chunks per streaming item (16 rows)
+
+struct TrsvSync {
+    unsigned bar_count, bar_gen, qhead, abort, ncrit, pad[3];
+    // followed by ycnt[nbi], updcnt[nbi], chunk[nbi * CH] (unsigned)
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *p >= target (bounded); the CTA learns the outcome.
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target, TrsvSync *sy, MpDevStatus *st,
+                                         bool *abort_s) {
+    if (threadIdx.x == 0) {
+        if (ld_acquire(p) < target) {
+            const unsigned long long t0 = global_ns();
+            long long polls = 0;
+            while (ld_acquire(p) < target) {
+                if (ld_acquire(&sy->abort) || ++polls > (1LL << 24) || global_ns() - t0 > 1000000000ULL) {
+                    if (!ld_acquire(&sy->abort)) {
+                        mp_flag(st, MP_FLAG_TIMEOUT);
+                        atomicExch(&st->timeout_site, 2);
+                        atomicExch(&sy->abort, 1u);
+                    }
+                    *abort_s = true;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    __syncthreads();
+    return !*abort_s;
+}
+
+// acc[rows] -= F[rows, block] v for the rows [ra, rb) (a warp per row).
+template <typename T, int NR>
+__device__ __forceinline__ void update_rows(const T *F, long ldf, int coff, int bs, const T *vs, int BI, int nrhs,
+                                            int ra, int rb, T *acc, int n, bool stream) {
+    const int lane = threadIdx.x & 31;
+    for (int r = ra + (threadIdx.x >> 5); r < rb; r += kThreads / 32) {
+        T sum[NR];
+        if (stream)
+            row_dot<T, true, NR>(F + (long)r * ldf + coff, bs, vs, BI, nrhs, sum);
+        else
+            row_dot<T, false, NR>(F + (long)r * ldf + coff, bs, vs, BI, nrhs, sum);
+        if (lane == 0)
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+                if (h < nrhs) acc[(long)h * n + r] -= sum[h];
+    }
+}
+
+// nrhs vectors of the block [r0, r0 + bs) into shared memory (stride BI,
+// zero beyond bs), past L1: other CTAs wrote them in this launch.
+template <typename T>
+__device__ __forceinline__ void stage_vec(const T *src, long ld, int r0, int bs, int BI, int nrhs, T *vs) {
+    for (int idx = threadIdx.x; idx < nrhs * BI; idx += kThreads) {
+        const int h = idx / BI, k = idx - h * BI;
+        vs[idx] = k < bs ? __ldcg(src + (long)h * ld + r0 + k) : T(0);
+    }
+    __syncthreads();
+}
+
 template <typename T, bool LOWER, int NR>
 __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
-trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ldw, const T *__restrict__ Inv,
-                       const double *__restrict__ R, long ldr, const int *__restrict__ perm,
-                       const double *__restrict__ rnorm, const T *__restrict__ Yin, long ldyin,
-                       T *__restrict__ Yout, long ldyout, T *__restrict__ acc, unsigned *bar_count,
-                       unsigned *bar_gen, MpDevStatus *st) {
+trsv_dataflow_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ldw, const T *__restrict__ Inv,
+                     const double *__restrict__ R, long ldr, const int *__restrict__ perm,
+                     const double *__restrict__ rnorm, const T *__restrict__ Yin, long ldyin,
+                     T *__restrict__ Yout, long ldyout, T *__restrict__ acc, unsigned *sync, int crit_sms,
+                     MpDevStatus *st) {
     extern __shared__ __align__(16) unsigned char raw[];
     T *vs = reinterpret_cast<T *>(raw);  // nrhs x BI vector of the current block
     __shared__ bool abort_s;
-    if (threadIdx.x == 0) abort_s = false;
-    const int lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * (kThreads / 32);
+    __shared__ unsigned item_s, crit_s;
+    TrsvSync *sy = reinterpret_cast<TrsvSync *>(sync);
+    const int nbi = (n + BI - 1) / BI, CH = BI / kRC;
+    unsigned *ycnt = sync + 8, *updcnt = ycnt + nbi, *chunk = updcnt + nbi;
+    // the chain's group: the CTAs resident on the first crit_sms SMs, so
+    // that no streaming CTA competes with them for an SM's load bandwidth
+    if (threadIdx.x == 0) {
+        abort_s = false;
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        crit_s = (int)smid < crit_sms ? atomicAdd(&sy->ncrit, 1u) : 0xFFFFFFFFu;
+    }
     const long gtid = (long)blockIdx.x * kThreads + threadIdx.x;
     const long gthreads = (long)gridDim.x * kThreads;
-    const int nbi = (n + BI - 1) / BI;
+    auto block_of = [&](int s) { return LOWER ? s : nbi - 1 - s; };
 
     // acc = right-hand side (P r / s for L; y for U)
     for (long idx = gtid; idx < (long)nrhs * n; idx += gthreads) {
@@ -156,46 +249,100 @@ trsv_persistent_kernel(int n, int nrhs, int BI, const T *__restrict__ W, long ld
         }
         acc[(long)h * n + r] = v;
     }
-    if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
-
-    for (int step = 0; step < nbi; ++step) {
-        const int b = LOWER ? step : nbi - 1 - step;
-        const int r0 = b * BI;
-        const int bs = min(BI, n - r0);
-        // ---- A: y_b = inv(D_b) acc_b
-        for (int idx = threadIdx.x; idx < nrhs * BI; idx += kThreads) {
-            const int h = idx / BI, k = idx - h * BI;
-            vs[idx] = k < bs ? __ldcg(acc + (long)h * n + r0 + k) : T(0);
+    if (!grid_barrier(&sy->bar_count, &sy->bar_gen, st, &abort_s)) return;
+    int ncrit = (int)ld_acquire(&sy->ncrit);
+    int ci = (int)crit_s;
+    if (ncrit == 0 || ncrit >= (int)gridDim.x) {  // placement left no split: decide by index
+        ncrit = max(1, min(CH, (int)gridDim.x / 4));
+        ci = (int)blockIdx.x < ncrit ? (int)blockIdx.x : -1;
+    }
+    if (ci >= 0 && ci < ncrit) {
+        // ---- the chain: A(s), then near(s), for every step
+        for (int s = 0; s < nbi; ++s) {
+            const int b = block_of(s), r0 = b * BI, bs = min(BI, n - r0);
+            const T *D = Inv + (long)b * BI * BI;
+            if (!wait_geq(&updcnt[b], (unsigned)(s * CH), sy, st, &abort_s)) return;
+            stage_vec<T>(acc, n, r0, bs, BI, nrhs, vs);
+            unsigned mine = 0;
+            for (int j = ci; j < CH; j += ncrit) {
+                const int ra = min(bs, j * kRC), rb = min(bs, ra + kRC);
+                const int lane = threadIdx.x & 31;
+                for (int r = ra + (threadIdx.x >> 5); r < rb; r += kThreads / 32) {
+                    T sum[NR];
+                    row_dot<T, false, NR>(D + (long)r * BI, bs, vs, BI, nrhs, sum);
+                    if (lane == 0)
+#pragma unroll
+                        for (int h = 0; h < NR; ++h)
+                            if (h < nrhs) Yout[(long)h * ldyout + r0 + r] = sum[h];
+                }
+                ++mine;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && mine) {
+                __threadfence();
+                atomicAdd(&ycnt[b], mine);
+            }
+            if (s + 1 == nbi) break;
+            // near(s): the next block's rows
+            const int c = block_of(s + 1), c0 = c * BI, cs = min(BI, n - c0);
+            if (!wait_geq(&ycnt[b], (unsigned)CH, sy, st, &abort_s)) return;
+            stage_vec<T>(Yout, ldyout, r0, bs, BI, nrhs, vs);
+            for (int j = ci; j < CH; j += ncrit) {
+                if (!wait_geq(&chunk[c * CH + j], (unsigned)s, sy, st, &abort_s)) return;
+                const int ra = min(cs, j * kRC), rb = min(cs, ra + kRC);
+                update_rows<T, NR>(W, ldw, r0, bs, vs, BI, nrhs, c0 + ra, c0 + rb, acc, n, true);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release(&chunk[c * CH + j], (unsigned)(s + 1));
+                    atomicAdd(&updcnt[c], 1u);
+                }
+            }
+        }
+        return;
+    }
+    // ---- the far updates: items (s, t, j), t >= s + 2, taken in order
+    const int NG = (CH + kFG - 1) / kFG;  // streaming items per block
+    const long nfar = nbi >= 3 ? (long)(nbi - 2) * (nbi - 1) / 2 * NG : 0;
+    int staged = -1;
+    // the next item is claimed while the current one is processed
+    if (threadIdx.x == 0) item_s = atomicAdd(&sy->qhead, 1u);
+    __syncthreads();
+    long q = item_s;
+    __syncthreads();
+    for (;;) {
+        if (q >= nfar) break;
+        unsigned next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&sy->qhead, 1u);
+        // decode: step s has (nbi - s - 2) * NG items
+        long rem = q;
+        int s = 0;
+        while (rem >= (long)(nbi - s - 2) * NG) {
+            rem -= (long)(nbi - s - 2) * NG;
+            ++s;
+        }
+        const int t = s + 2 + (int)(rem / NG), j0 = (int)(rem % NG) * kFG, j1 = min(CH, j0 + kFG);
+        const int b = block_of(s), r0 = b * BI, bs = min(BI, n - r0);
+        const int c = block_of(t), c0 = c * BI, cs = min(BI, n - c0);
+        if (staged != s) {
+            if (!wait_geq(&ycnt[b], (unsigned)CH, sy, st, &abort_s)) return;
+            stage_vec<T>(Yout, ldyout, r0, bs, BI, nrhs, vs);
+            staged = s;
+        }
+        for (int j = j0; j < j1; ++j)
+            if (!wait_geq(&chunk[c * CH + j], (unsigned)s, sy, st, &abort_s)) return;
+        const int ra = min(cs, j0 * kRC), rb = min(cs, j1 * kRC);
+        update_rows<T, NR>(W, ldw, r0, bs, vs, BI, nrhs, c0 + ra, c0 + rb, acc, n, true);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            for (int j = j0; j < j1; ++j) st_release(&chunk[c * CH + j], (unsigned)(s + 1));
+            atomicAdd(&updcnt[c], (unsigned)(j1 - j0));
+            item_s = next;
         }
         __syncthreads();
-        const T *D = Inv + (long)b * BI * BI;
-        for (int r = gwarp; r < bs; r += nwarps) {
-            T sum[NR];
-            row_dot<T, false, NR>(D + (long)r * BI, bs, vs, BI, nrhs, sum);
-            if (lane == 0)
-#pragma unroll
-                for (int h = 0; h < NR; ++h)
-                    if (h < nrhs) Yout[(long)h * ldyout + r0 + r] = sum[h];
-        }
-        if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
-        // ---- B: acc_r -= W[r, block b] y_b for the rows still to be solved
-        const int lo = LOWER ? r0 + bs : 0;
-        const int hi = LOWER ? n : r0;
-        if (lo >= hi) continue;  // last step: nothing left to update
-        for (int idx = threadIdx.x; idx < nrhs * BI; idx += kThreads) {
-            const int h = idx / BI, k = idx - h * BI;
-            vs[idx] = k < bs ? __ldcg(Yout + (long)h * ldyout + r0 + k) : T(0);
-        }
+        q = item_s;
         __syncthreads();
-        for (int r = lo + gwarp; r < hi; r += nwarps) {
-            T sum[NR];
-            row_dot<T, true, NR>(W + (long)r * ldw + r0, bs, vs, BI, nrhs, sum);
-            if (lane == 0)
-#pragma unroll
-                for (int h = 0; h < NR; ++h)
-                    if (h < nrhs) acc[(long)h * n + r] -= sum[h];
-        }
-        if (!grid_barrier(bar_count, bar_gen, st, &abort_s)) return;
     }
 }
 
@@ -213,16 +360,17 @@ int num_sms_cached() {
 template <typename T, bool LOWER>
 cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, const T *Inv, const double *R, long ldr,
                               const int *perm, const double *rnorm, const T *Yin, long ldyin, T *Yout, long ldyout,
-                              T *acc, unsigned *bar, MpDevStatus *st, cudaStream_t s) {
+                              T *acc, unsigned *sync, MpDevStatus *st, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     if (nrhs > kMaxRhs) return cudaErrorInvalidValue;
     // the right-hand-side count padded to 1, 2, 4 or 8 (fewer registers, so
     // more rows in flight per SM)
-    auto kern = nrhs <= 1 ? trsv_persistent_kernel<T, LOWER, 1>
-                          : nrhs <= 2 ? trsv_persistent_kernel<T, LOWER, 2>
-                                      : nrhs <= 4 ? trsv_persistent_kernel<T, LOWER, 4>
-                                                  : trsv_persistent_kernel<T, LOWER, 8>;
-    const size_t smem = sizeof(T) * (size_t)(nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8) * BI;
+    auto kern = nrhs <= 1 ? trsv_dataflow_kernel<T, LOWER, 1>
+                          : nrhs <= 2 ? trsv_dataflow_kernel<T, LOWER, 2>
+                                      : nrhs <= 4 ? trsv_dataflow_kernel<T, LOWER, 4>
+                                                  : trsv_dataflow_kernel<T, LOWER, 8>;
+    const int nr = nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8;
+    const size_t smem = sizeof(T) * (size_t)nr * BI;  // the vector of the current block
     cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -230,11 +378,15 @@ cudaError_t launch_persistent(int n, int nrhs, int BI, const T *W, long ldw, con
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = num_sms_cached() * std::min(per_sm, 4);
-    unsigned *cnt = bar, *gen = bar + 1;
-    void *args[] = {(void *)&n,    (void *)&nrhs,  (void *)&BI,    (void *)&W,    (void *)&ldw,
-                    (void *)&Inv,  (void *)&R,     (void *)&ldr,   (void *)&perm, (void *)&rnorm,
+    // the chain's group: the CTAs on a quarter of the SMs
+    int crit_sms = std::max(1, num_sms_cached() / 4);
+    if (grid < 2) return cudaErrorInvalidConfiguration;
+    e = cudaMemsetAsync(sync, 0, trsv_sync_bytes<T>(n), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&n,    (void *)&nrhs,  (void *)&BI,    (void *)&W,      (void *)&ldw,
+                    (void *)&Inv,  (void *)&R,     (void *)&ldr,   (void *)&perm,   (void *)&rnorm,
                     (void *)&Yin,  (void *)&ldyin, (void *)&Yout,  (void *)&ldyout, (void *)&acc,
-                    (void *)&cnt,  (void *)&gen,   (void *)&st};
+                    (void *)&sync, (void *)&crit_sms, (void *)&st};
     mp_note_launch();
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), args, smem, s);
 }
@@ -280,6 +432,15 @@ size_t trsv_inverse_bytes(int n) {
 }
 template size_t trsv_inverse_bytes<float>(int);
 template size_t trsv_inverse_bytes<double>(int);
+
+template <typename T>
+size_t trsv_sync_bytes(int n) {
+    const int BI = trsv_inverse_block<T>(n);
+    const size_t nbi = (size_t)(std::max(n, 1) + BI - 1) / BI;
+    return sizeof(unsigned) * (8 + 2 * nbi + nbi * (size_t)(BI / kRC));
+}
+template size_t trsv_sync_bytes<float>(int);
+template size_t trsv_sync_bytes<double>(int);
 
 template <typename T>
 size_t trsv_tmp_bytes(int n) {
