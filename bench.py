@@ -331,7 +331,7 @@ def run_secondary(args):
 CLASS_KERNEL = {"panel": ("panel_getf2_kernel", "paper_0808_2794_gb300/csrc/panel.cu"),
                 "panelgemm": ("leaf_update_persistent_kernel", "paper_0808_2794_gb300/csrc/blas3.cu"),
                 "update": ("tc_update_kernel", "paper_0808_2794_gb300/csrc/tc_gemm.cu"),
-                "trsv": ("trsv_persistent_kernel", "paper_0808_2794_gb300/csrc/trsv.cu"),
+                "trsv": ("trsv_dataflow_kernel", "paper_0808_2794_gb300/csrc/trsv.cu"),
                 "residual": ("residual_partial_kernel", "paper_0808_2794_gb300/csrc/refine.cu")}
 
 
