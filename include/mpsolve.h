@@ -183,7 +183,7 @@ MP_API int mp_gesv_batched(int batch, const int *n, const int *nrhs, const doubl
                            size_t work_bytes, const mp_opts *opts, void *stream);
 
 /* Tile schedule of the batched solver (no counterpart in the paper): the
- * panel width (8, 16 or 32 columns) of each system's low-precision
+ * panel width (8 or 16 columns) of each system's low-precision
  * factorization by range of n.  Range i covers nmax[i-1] < n <= nmax[i]
  * (nmax increasing, the last >= MP_BATCH_MAX_N).  The library starts from
  * a table chosen on GB300 by the project's autotuner, which times every

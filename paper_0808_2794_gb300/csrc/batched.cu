@@ -49,7 +49,7 @@ template <typename T> using V16 = typename V16Of<T>::type;
 template <typename T> constexpr int VW16 = 16 / (int)sizeof(T);
 
 template <typename T> struct BCfg;
-template <> struct BCfg<float> { static constexpr int NB = 32; };
+template <> struct BCfg<float> { static constexpr int NB = 16; };
 template <> struct BCfg<double> { static constexpr int NB = 16; };
 
 
@@ -92,7 +92,7 @@ constexpr size_t batched_smem_bytes() {
            + sizeof(double) * (size_t)kMaxN * kMaxRhs // x (FP64) for the residual
            + sizeof(Shared);                          // reductions, scalars, row moves
 }
-static_assert((sizeof(float) * (size_t)kMaxN * 33 + sizeof(float) * 32 * kMaxN) % 8 == 0, "alignment");
+static_assert((sizeof(float) * (size_t)kMaxN * 17 + sizeof(float) * 16 * kMaxN) % 8 == 0, "alignment");
 static_assert((sizeof(double) * (size_t)kMaxN * 17 + sizeof(double) * 16 * kMaxN) % 8 == 0, "alignment");
 
 // Block-wide max of a non-negative double (NaN counts as +inf).
@@ -440,7 +440,7 @@ __device__ __forceinline__ void residual_rows(const BatchSys &d, int n, int nrhs
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
 batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int count, int *counter, int prec,
                int itermax, double tol, double stall_ratio) {
     constexpr int NB = BCfg<T>::NB;
@@ -527,8 +527,7 @@ batched_kernel(BatchSys *__restrict__ sys, const int *__restrict__ order, int co
         // ---- factor
         if constexpr (sizeof(T) == 4) {  // the panel width the schedule gave this system
             if (d.nb == 8) lu_factor<T, 8>(d, W, ldw, P, Us, sh, prec);
-            else if (d.nb == 16) lu_factor<T, 16>(d, W, ldw, P, Us, sh, prec);
-            else lu_factor<T, 32>(d, W, ldw, P, Us, sh, prec);
+            else lu_factor<T, NB>(d, W, ldw, P, Us, sh, prec);  // the buffers' width bounds the panel
         } else {
             lu_factor<T, NB>(d, W, ldw, P, Us, sh, prec);
         }
@@ -652,10 +651,12 @@ cudaError_t launch_batched(BatchSys *dsys, const int *dorder, int count, int *dc
     auto kern = batched_kernel<T>;
     cudaError_t e = mp_smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(count, std::max(sms, 1));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(count, std::max(sms, 1) * std::max(per_sm, 1));
     e = cudaMemsetAsync(dcounter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     mp_note_launch();
@@ -693,7 +694,7 @@ int schedule_nb(int n) {
     std::lock_guard<std::mutex> g(g_sched_mu);
     for (size_t i = 0; i < g_sched_nmax.size(); ++i)
         if (n <= g_sched_nmax[i]) return g_sched_nb[i];
-    return 32;
+    return 16;
 }
 }  // namespace
 
@@ -709,7 +710,7 @@ extern "C" int mp_batched_set_schedule(int count, const int *nmax, const int *nb
     if (!nb) return mp_arg_fail(3, "nb is NULL");
     for (int i = 0; i < count; ++i) {
         if (nmax[i] < 1 || (i > 0 && nmax[i] <= nmax[i - 1])) return mp_arg_fail(2, "nmax must increase");
-        if (nb[i] != 8 && nb[i] != 16 && nb[i] != 32) return mp_arg_fail(3, "nb must be 8, 16 or 32");
+        if (nb[i] != 8 && nb[i] != 16) return mp_arg_fail(3, "nb must be 8 or 16");
     }
     if (nmax[count - 1] < MP_BATCH_MAX_N) return mp_arg_fail(2, "the last range must reach MP_BATCH_MAX_N");
     g_sched_nmax.assign(nmax, nmax + count);

@@ -1,7 +1,7 @@
 """Autotuner of the batched solver's tile schedule.
 
 The batched solver factors each small system inside one CTA with a blocked
-LU whose panel width (8, 16 or 32 columns) trades the latency-bound pivoted
+LU whose panel width (8 or 16 columns) trades the latency-bound pivoted
 panel against the trailing update.  For every range of n of the built-in
 schedule this script times, on the GPU, the systems of the config-4 batch
 (4096 systems, n log-uniform in [16, 512], nrhs 1..4) that fall in the range,
@@ -19,7 +19,7 @@ import os
 
 import numpy as np
 
-CANDIDATES = (8, 16, 32)
+CANDIDATES = (8, 16)
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 

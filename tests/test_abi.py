@@ -78,7 +78,7 @@ def test_batched_schedule_set_get_and_validation():
     from paper_0808_2794_gb300 import solver
     base = solver.batched_schedule()
     assert base and base[-1][0] >= solver.BATCH_MAX_N
-    assert all(nb in (8, 16, 32) for _, nb in base)
+    assert all(nb in (8, 16) for _, nb in base)
     try:
         solver.set_batched_schedule([(64, 8), (512, 16)])
         assert solver.batched_schedule() == [(64, 8), (512, 16)]
