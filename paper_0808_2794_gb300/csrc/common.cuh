@@ -46,6 +46,48 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 // element-wise, round to nearest even): d = a * b + c lane by lane, the same
 // bits as two fmaf calls.  The builtin lets the register allocator keep the
 // operands in register pairs.
+// fl32(v): v rounded to binary32, to nearest with ties to even, computed
+// from the IEEE 754 binary64 and binary32 encodings with 32-bit integer
+// operations only.  GB300's FP64 pipe issues a small fraction of the integer
+// rate, so an n^2 conversion that converts with the FP64 unit is bound by it
+// rather than by HBM.  Normal results take the first branch: keep 23 of the 52
+// fraction bits, round on the 29 dropped ones (a carry out of the fraction
+// raises the exponent, and from the largest exponent gives infinity).
+static __device__ __noinline__ uint32_t fl32_bits_rare(uint32_t hi, uint32_t lo) {
+    const uint32_t sign = hi & 0x80000000u;
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    const uint32_t frac_hi = hi & 0xfffffu;
+    if (ex == 0x7ff)  // infinity, or NaN (quiet, keeping the top payload bits)
+        return (frac_hi | lo) ? (sign | 0x7fc00000u | (frac_hi << 3) | (lo >> 29)) : (sign | 0x7f800000u);
+    if (ex >= 1151) return sign | 0x7f800000u;  // |v| >= 2^128: beyond the largest binary32 after rounding
+    // binary32 subnormal or zero: the significand in units of 2^-149
+    const unsigned long long M = ((unsigned long long)(ex ? (frac_hi | 0x100000u) : frac_hi) << 32) | lo;
+    const int sh = ex ? 926 - ex : 925;  // >= 30 here
+    if (sh > 63) return sign;  // |v| < 2^-150: rounds to zero
+    unsigned long long q = M >> sh;
+    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    return sign | (uint32_t)q;  // 2^23 after rounding is the smallest normal
+}
+
+__device__ __forceinline__ float fl32_rne(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t fe = ((hi >> 20) & 0x7ffu) - 896u;  // binary32 biased exponent (wraps when below 1)
+    if (fe - 1u < 254u) {
+        uint32_t f = (fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t r = lo & 0x1fffffffu;
+        f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+        return __uint_as_float((hi & 0x80000000u) | f);
+    }
+    return __uint_as_float(fl32_bits_rare(hi, lo));
+}
+
+// v is infinite or NaN (exponent field all ones), tested on the high word
+__device__ __forceinline__ bool nonfinite_f64(double v) {
+    return ((uint32_t)__double2hiint(v) & 0x7ff00000u) == 0x7ff00000u;
+}
+
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {

@@ -5,7 +5,8 @@
 // A (FP64, column-major, the caller's) is read once, coalesced, through a
 // 64x64 shared-memory transpose into the row-major W; row sums of |a_ij| are
 // accumulated for ||A||_inf, and any NaN/Inf raises MP_FLAG_NONFINITE_INPUT.
-// Conversion to FP32 is round-to-nearest-even (__double2float_rn).
+// Conversion to FP32 is round-to-nearest-even (fl32_rne: integer operations;
+// the FP64 pipe is left to the row sums, one add per element).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -16,7 +17,7 @@ constexpr int kColTiles = 4;  // each CTA walks 4 column tiles: fewer row-sum at
 
 template <typename Tout>
 __device__ __forceinline__ Tout cvt(double v);
-template <> __device__ __forceinline__ float cvt<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ float cvt<float>(double v) { return fl32_rne(v); }
 template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
 
 // 64 x 64 tiles: a warp reads 64 rows of a column as 16-byte pieces (512
@@ -56,8 +57,7 @@ convert_transpose_kernel(int n, const double *__restrict__ A, long lda, Tout *__
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            if (!(fabs(v[q].x) <= 1.79769313486231570815e308) || !(fabs(v[q].y) <= 1.79769313486231570815e308))
-                bad = true;
+            bad |= nonfinite_f64(v[q].x) | nonfinite_f64(v[q].y);
             rsum0 += fabs(v[q].x);
             rsum1 += fabs(v[q].y);
             tile[warp + 8 * q][2 * lane] = cvt<Tout>(v[q].x);
@@ -116,7 +116,7 @@ convert_lower_kernel(int n, const double *__restrict__ A, long lda, Tout *__rest
         const int c = c0 + ty + 8 * q, r = r0 + tx;
         double v = 0.0;
         if (r < n && c <= r) v = A[(long)c * lda + r];
-        if (!(fabs(v) <= 1.79769313486231570815e308)) bad = true;
+        bad |= nonfinite_f64(v);
         rsum += fabs(v);
         // strictly lower entries also count for row c: reduce over the 32 rows r
         double cs = (r > c) ? fabs(v) : 0.0;

@@ -80,6 +80,48 @@ def test_convert_bitexact(torch, mp, orc, n):
     assert host(flags)[0] & mp.FLAG_NONFINITE_INPUT
 
 
+def _special_doubles(n, seed):
+    """n x n FP64 values that reach every branch of round-to-nearest-even into
+    binary32: uniformly random bit patterns (all exponents: overflow, the
+    binary32 subnormal range, binary64 subnormals, infinities, NaNs), exact
+    ties between adjacent binary32 values (normal and subnormal), the
+    neighbours of every tie, the overflow threshold and signed zeros."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2 ** 63, size=n * n, dtype=np.int64).astype(np.uint64)
+    bits |= rng.integers(0, 2, size=n * n).astype(np.uint64) << np.uint64(63)
+    v = bits.view(np.float64).copy()
+    m = n * n // 2
+    f = rng.standard_normal(m // 3).astype(np.float32) * np.float32(2.0) ** rng.integers(-140, 120, m // 3)
+    f = np.where(np.isfinite(f) & (f != 0), f, np.float32(1.5))
+    g = np.nextafter(f, np.float32(np.inf))
+    tie = (f.astype(np.float64) + g.astype(np.float64)) / 2.0  # exact in binary64
+    around = np.concatenate([tie, np.nextafter(tie, np.inf), np.nextafter(tie, -np.inf)])
+    v[: around.size] = around
+    fmax = float(np.finfo(np.float32).max)
+    ulp = fmax - float(np.nextafter(np.float32(fmax), np.float32(0)))
+    edge = [fmax, fmax + ulp / 2, np.nextafter(fmax + ulp / 2, 0), np.nextafter(fmax + ulp / 2, np.inf),
+            2.0 ** -149, 2.0 ** -150, np.nextafter(2.0 ** -150, 1), 3 * 2.0 ** -151, 2.0 ** -126,
+            np.nextafter(2.0 ** -126, 0), 0.0, -0.0, 5e-324, np.inf, -np.inf, np.nan]
+    v[around.size: around.size + len(edge)] = edge
+    v[around.size + len(edge): around.size + 2 * len(edge)] = -np.array(edge)
+    return np.asfortranarray(v.reshape(n, n))
+
+
+def test_convert_rounding_special_values(torch, mp):
+    """fl32 of every class of binary64 value, bit for bit against the host's
+    IEEE conversion (numpy, round to nearest even); NaN maps to NaN."""
+    n = 96
+    A = _special_doubles(n, seed=7)
+    with np.errstate(over="ignore", invalid="ignore"):
+        want = A.astype(np.float32)
+    W, _, flags = mp.convert(dev(torch, A))
+    W = host(W)[:, :n]
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(W), nan)
+    assert np.array_equal(W[~nan].view(np.uint32), want[~nan].view(np.uint32))
+    assert host(flags)[0] & mp.FLAG_NONFINITE_INPUT
+
+
 # ------------------------------------------------ a2-a4: panel, swaps, TRSM
 
 def _factor(torch, mp, A, prec="fp32", nb_outer=0):
