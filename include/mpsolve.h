@@ -470,6 +470,10 @@ MP_API int mp_selftest_wait_timeout(int site, unsigned long long limit_ns, void 
  * mask (bit i = class i) on the stream each kernel is launched on, and
  * clears the accumulated records. */
 MP_API void mp_profile_enable(unsigned mask);
+/* Times one launch in every `every` (>= 1; default 1 = all) of each enabled
+ * class, counting from the last mp_profile_enable or mp_profile_sample call,
+ * so that the events add little to a latency-bound chain of launches. */
+MP_API void mp_profile_sample(int every);
 /* Waits for the recorded events and returns, per class, the summed kernel
  * time (ms), the number of timed launches and the summed algorithmic work of
  * those launches (flops for PANEL/TRSM/UPDATE/PANELGEMM, bytes for the

@@ -64,6 +64,8 @@ struct ProfRec {
 };
 std::mutex g_prof_mu;
 unsigned g_prof_mask = 0;
+int g_prof_every = 1;                            // record one scope in every g_prof_every of a class
+std::atomic<unsigned> g_prof_seen[MP_KC_COUNT];  // scopes of each class met since the last enable
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_prof_pool;  // recorded-and-read events, reused (creating one costs host time)
 
@@ -87,7 +89,8 @@ void prof_release(const ProfRec &r) {
 }  // namespace
 
 MpProfScope::MpProfScope(int cls_, double work_, cudaStream_t s_) : cls(cls_), work(work_), s(s_) {
-    if (g_prof_mask & (1u << cls)) {
+    if ((g_prof_mask & (1u << cls)) &&
+        (g_prof_every <= 1 || g_prof_seen[cls].fetch_add(1, std::memory_order_relaxed) % g_prof_every == 0)) {
         e0 = prof_event();
         if (e0) cudaEventRecord(e0, s);
     }
@@ -135,6 +138,13 @@ extern "C" void mp_profile_enable(unsigned mask) {
     }
     g_prof.clear();
     g_prof_mask = mask;
+    for (auto &c : g_prof_seen) c.store(0, std::memory_order_relaxed);
+}
+
+extern "C" void mp_profile_sample(int every) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_every = every < 1 ? 1 : every;
+    for (auto &c : g_prof_seen) c.store(0, std::memory_order_relaxed);
 }
 
 extern "C" int mp_profile_collect(double *ms, long long *launches, double *work) {

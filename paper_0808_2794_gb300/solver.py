@@ -125,6 +125,7 @@ _SIGS = {
     "mp_selftest_wait_timeout": (_I, [_I, ctypes.c_ulonglong, _P, _Z, ctypes.POINTER(ctypes.c_uint),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
     "mp_profile_enable": (None, [ctypes.c_uint]),
+    "mp_profile_sample": (None, [ctypes.c_int]),
     "mp_profile_collect": (_I, [_P, _P, _P]),
     "mp_launch_count": (ctypes.c_longlong, []),
 }
@@ -138,6 +139,11 @@ def profile_enable(classes=()):
     for c in classes:
         mask |= 1 << KERNEL_CLASSES.index(c)
     load().mp_profile_enable(mask)
+
+
+def profile_sample(every=1):
+    """Time one launch in every `every` of each enabled class (1: all)."""
+    load().mp_profile_sample(int(every))
 
 
 def profile_collect():
