@@ -100,9 +100,6 @@ typedef struct {
     int allow_fallback;  /* re-factor in FP64 on breakdown/stall/non-convergence (default 1) */
     int nb_outer;        /* outer block width of the factorization (0 = auto; 32..1024) */
     int nb_inner;        /* reserved (0 = auto) */
-    int lookahead;       /* outer look-ahead of the LU factorization on the tensor-core rungs: the
-                            trailing update of one outer panel overlaps the factorization of the
-                            next (-1 = auto, 0 = off, 1 = on) */
 } mp_opts;
 
 typedef struct {
@@ -467,9 +464,7 @@ MP_API int mp_selftest_wait_timeout(int site, unsigned long long limit_ns, void 
 #define MP_KC_PANELGEMM 4  /* FP32 updates inside the recursive panel */
 #define MP_KC_TRSV 5       /* triangular solves with the factors */
 #define MP_KC_RESIDUAL 6   /* FP64 residual */
-#define MP_KC_LOOKAHEAD 7  /* the outer look-ahead's step between two panels on the critical path
-                              (waiting for the concurrent update included; work 0) */
-#define MP_KC_COUNT 8
+#define MP_KC_COUNT 7
 
 /* Enables (mask != 0) or disables event timing of the kernel classes in
  * mask (bit i = class i) on the stream each kernel is launched on, and

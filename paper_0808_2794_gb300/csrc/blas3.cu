@@ -474,15 +474,14 @@ __global__ void __launch_bounds__(512, 1) leaf_update_persistent_kernel(const Le
     constexpr int CWm = kMoveBytes / sizeof(T);
     T *W = p.W;
     const long ld = p.ld;
-    const int k = p.k, kb = p.kb, coff = p.coff, N = p.N, M = p.M, mc0 = p.mc0, mc1 = p.mc1, mc2 = p.mc2,
-              mc3 = p.mc3;
+    const int k = p.k, kb = p.kb, coff = p.coff, N = p.N, M = p.M, mc1 = p.mc1, mc2 = p.mc2, mc3 = p.mc3;
     const int2 *pairs = p.pairs;
     int *perm = p.perm;
     const int tid = threadIdx.x;
     const int NU = (p.kbp > 0 && p.tc1 > p.tc0) ? (p.tc1 - p.tc0 + TrsmTile<T, KBMAX>::CW - 1) / TrsmTile<T, KBMAX>::CW
                                                   : 0;
     const int R = max(1, (M + 127) / 128), C = (N > 0 && kb > 0) ? (N + kLeafTileCols - 1) / kLeafTileCols : 0;
-    const int n1 = mc1 > mc0 ? (mc1 - mc0 + CWm - 1) / CWm : 0, n2 = mc3 > mc2 ? (mc3 - mc2 + CWm - 1) / CWm : 0;
+    const int n1 = (mc1 + CWm - 1) / CWm, n2 = mc3 > mc2 ? (mc3 - mc2 + CWm - 1) / CWm : 0;
     const int np = p.npairs ? min(*p.npairs, 2 * KBMAX) : 0;
     const int nitems = NU + R * C + (np > 0 ? n1 + n2 : 0) + (perm && np > 0 ? 1 : 0);
     if ((int)blockIdx.x >= nitems) return;
@@ -516,14 +515,13 @@ __global__ void __launch_bounds__(512, 1) leaf_update_persistent_kernel(const Le
                                            bits, stage);
         } else if (t2 < R * C + n1 + n2) {
             const int q = t2 - R * C;
-            const int cs = q < n1 ? mc0 + q * CWm : mc2 + (q - n1) * CWm;
+            const int cs = q < n1 ? q * CWm : mc2 + (q - n1) * CWm;
             const int ce = q < n1 ? min(cs + CWm, mc1) : min(cs + CWm, mc3);
             using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
             constexpr int VW = 16 / sizeof(T), NV = CWm / VW;
             V *tile = reinterpret_cast<V *>(stage);
-            // cs is a multiple of the vector width (mc0 and mc2 are) and ld
-            // of 32, so a vector is either wholly inside [cs, ce) or (at the
-            // ragged end) read by elements
+            // cs is a multiple of CWm and ld of 32, so a vector is either
+            // wholly inside [cs, ce) or (at the ragged end) read by elements
             for (int idx = tid; idx < np * NV; idx += blockDim.x) {
                 const int pr = idx / NV, c = cs + (idx - pr * NV) * VW;
                 const T *src = W + (long)pairs[pr].y * ld + c;
@@ -553,81 +551,6 @@ __global__ void __launch_bounds__(512, 1) leaf_update_persistent_kernel(const Le
             for (int i = tid; i < np; i += blockDim.x) perm[pairs[i].x] = pv[i];
         }
         __syncthreads();  // the shared arrays are reused by the next item
-    }
-}
-
-// One step of the outer look-ahead on 32-column chunks of W: chunks of
-// [m0, m1) get the outer panel's row moves only (leaf by leaf: every source
-// row of a leaf is read into shared memory before any destination row is
-// written, as the moves of one leaf form cycles); chunks of [c0, c1) get the
-// moves, then U12 = L11^{-1} A12 on the panel's rows [k, k + nbk) (L11 unit
-// lower, in W), then max |U12| raised into *umax (uint bits of a
-// non-negative float, NaN counted as infinite).  The solve is blocked by 32
-// rows in shared memory: warp 0 substitutes through the diagonal block (lane
-// = column, rows in order), then every thread updates its rows below with
-// that block's L columns in order, in FP32 (FP64) FMAs.
-constexpr int kLaCols = 32;
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-la_moves_trsm_kernel(T *__restrict__ W, long ld, int k, int nbk, const int2 *__restrict__ pairs,
-                     const int *__restrict__ npairs, int nleaves, int stride, int max_pairs, int m0, int m1, int c0,
-                     int c1, unsigned *umax) {
-    extern __shared__ __align__(16) unsigned char dyn_raw[];
-    T *tile = reinterpret_cast<T *>(dyn_raw);  // max_pairs x 32
-    T(*Ld)[kLaCols + 1] = reinterpret_cast<T(*)[kLaCols + 1]>(tile + (size_t)max_pairs * kLaCols);  // 32 x 33
-    T(*Bs)[kLaCols + 1] = Ld + kLaCols;                                                               // nbk x 33
-    const int nm = (m1 - m0 + kLaCols - 1) / kLaCols;
-    const bool solve = (int)blockIdx.x >= nm;
-    const int cs = solve ? c0 + ((int)blockIdx.x - nm) * kLaCols : m0 + (int)blockIdx.x * kLaCols;
-    const int ce = solve ? min(cs + kLaCols, c1) : min(cs + kLaCols, m1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, c = cs + lane;
-    for (int j = 0; j < nleaves; ++j) {
-        const int2 *pj = pairs + (long)j * stride;
-        const int np = min(npairs[j], max_pairs);
-        for (int r = warp; r < np; r += 8)
-            if (c < ce) tile[r * kLaCols + lane] = W[(long)pj[r].y * ld + c];
-        __syncthreads();
-        for (int r = warp; r < np; r += 8)
-            if (c < ce) W[(long)pj[r].x * ld + c] = tile[r * kLaCols + lane];
-        __syncthreads();
-    }
-    if (!solve) return;
-    for (int r = warp; r < nbk; r += 8) Bs[r][lane] = c < ce ? W[(long)(k + r) * ld + c] : T(0);
-    for (int jb = 0; jb < nbk; jb += kLaCols) {
-        const int h = min(kLaCols, nbk - jb);
-        for (int r = warp; r < h; r += 8) Ld[r][lane] = lane < h ? W[(long)(k + jb + r) * ld + k + jb + lane] : T(0);
-        __syncthreads();
-        if (warp == 0) {
-            for (int i = 1; i < h; ++i) {
-                T v = Bs[jb + i][lane];
-                for (int l = 0; l < i; ++l) v = fma(-Ld[i][l], Bs[jb + l][lane], v);
-                Bs[jb + i][lane] = v;
-            }
-        }
-        __syncthreads();
-        // rows below the block: B_i -= L_i,jb:jb+h B_jb:jb+h, l in order
-        for (int i = jb + h + warp; i < nbk; i += 8) {
-            const T *Li = W + (long)(k + i) * ld + k + jb;
-            T v = Bs[i][lane];
-            for (int l = 0; l < h; ++l) v = fma(-Li[l], Bs[jb + l][lane], v);
-            Bs[i][lane] = v;
-        }
-        __syncthreads();
-    }
-    float m = 0.f;
-    for (int r = warp; r < nbk; r += 8) {
-        if (c < ce) {
-            const T v = Bs[r][lane];
-            W[(long)(k + r) * ld + c] = v;
-            const float a = fabsf((float)v);
-            m = (a > m || a != a) ? ((a != a) ? INFINITY : a) : m;
-        }
-    }
-    if (umax) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-        if (lane == 0) atomicMax(umax, __float_as_uint(m));
     }
 }
 
@@ -703,8 +626,7 @@ cudaError_t launch_leaf_rest(const LeafRestArgs<T> &p, int clusters, int cluster
     static_assert(2 * KBMAX * kMoveBytes <= kLeafStageBytes, "exchange tile exceeds the staging area");
     static_assert(2 * KBMAX * kLeafTileCols * (int)sizeof(T) <= kLeafStageBytes, "moved rows exceed the staging area");
     if (p.kb < 0 || p.M < 0 || p.N < 0 || clusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
-    if (p.kb > KBMAX || p.N > 1024 || p.mc0 < 0 || p.mc1 < p.mc0 || p.mc3 < p.mc2 || p.M > kLeafMaxBitmapRows ||
-        (p.mc1 > p.mc0 && p.mc0 % (16 / (int)sizeof(T))) || (p.mc3 > p.mc2 && p.mc2 % (16 / (int)sizeof(T))))
+    if (p.kb > KBMAX || p.N > 1024 || p.mc1 < 0 || p.mc3 < p.mc2 || p.M > kLeafMaxBitmapRows)
         return cudaErrorInvalidValue;
     if (p.kb > 0 && p.N > 0 && !p.X) return cudaErrorInvalidValue;
     if (p.kbp < 0 || p.kbp > KBMAX || (p.kbp > 0 && (!p.Xp || p.kp < p.k0 || (p.kp - p.k0) % (16 / (int)sizeof(T)))))
@@ -776,31 +698,6 @@ template cudaError_t launch_apply_moves<float>(float *, long, const int2 *, cons
                                                int, int, int, int *, cudaStream_t);
 template cudaError_t launch_apply_moves<double>(double *, long, const int2 *, const int *, int,
                                                 int, int, int, int, int *, cudaStream_t);
-
-template <typename T>
-cudaError_t launch_la_moves_trsm(T *W, long ld, int k, int nbk, const int2 *pairs, const int *npairs, int nleaves,
-                                 int stride, int max_pairs, int m0, int m1, int c0, int c1, unsigned *umax,
-                                 cudaStream_t s) {
-    if (m1 < m0) m1 = m0;
-    if (c1 < c0) c1 = c0;
-    if (nleaves <= 0) m1 = m0;  // no moves: the chunks of [m0, m1) have nothing to do
-    const int nch = (m1 - m0 + kLaCols - 1) / kLaCols + (c1 - c0 + kLaCols - 1) / kLaCols;
-    if (nch == 0) return cudaSuccess;
-    if (nbk < 0 || nbk > 1024 || max_pairs < 0 || max_pairs > stride || (nleaves > 0 && (!pairs || !npairs)))
-        return cudaErrorInvalidValue;
-    const size_t smem = sizeof(T) * ((size_t)max_pairs * kLaCols + (size_t)(kLaCols + nbk) * (kLaCols + 1));
-    auto kern = la_moves_trsm_kernel<T>;
-    cudaError_t e = mp_smem_attr(kern, smem);
-    if (e != cudaSuccess) return e;
-    mp_note_launch();
-    kern<<<nch, 256, smem, s>>>(W, ld, k, nbk, pairs, npairs, std::max(0, nleaves), stride, max_pairs, m0, m1, c0, c1,
-                                umax);
-    return cudaGetLastError();
-}
-template cudaError_t launch_la_moves_trsm<float>(float *, long, int, int, const int2 *, const int *, int, int, int, int,
-                                                 int, int, int, unsigned *, cudaStream_t);
-template cudaError_t launch_la_moves_trsm<double>(double *, long, int, int, const int2 *, const int *, int, int, int,
-                                                  int, int, int, int, unsigned *, cudaStream_t);
 
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s) {

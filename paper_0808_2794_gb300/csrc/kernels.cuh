@@ -76,8 +76,7 @@ struct LeafRestArgs {
     unsigned *tickets = nullptr;
     const int2 *pairs = nullptr;
     const int *npairs = nullptr;
-    // the leaf's row exchange over the columns [mc0, mc1) and [mc2, mc3)
-    int mc0 = 0, mc1 = 0, mc2 = 0, mc3 = 0;
+    int mc1 = 0, mc2 = 0, mc3 = 0;
     int *perm = nullptr;
     // the previous leaf's U rows over the trailing columns (kbp = 0: none)
     const T *Xp = nullptr;
@@ -89,16 +88,6 @@ struct LeafRestArgs {
 template <typename T>
 cudaError_t launch_leaf_rest(const LeafRestArgs<T> &p, int clusters, int cluster, cudaStream_t s);
 template <typename T> int leaf_update_rest_clusters(int cluster);
-// The outer look-ahead's step on W, over 32-column chunks: the row moves of
-// `nleaves` consecutive leaves (leaf j's are pairs[j * stride ...], npairs[j]
-// of them, at most max_pairs, each a (destination, source) row), in leaf
-// order, over the columns [m0, m1) and [c0, c1); on [c0, c1) then
-// U12 = L11^{-1} A12 for the panel's rows [k, k + nbk) (L11 unit lower, in W)
-// with max |U12| raised into *umax (uint bits; may be NULL).  nbk <= 1024.
-template <typename T>
-cudaError_t launch_la_moves_trsm(T *W, long ld, int k, int nbk, const int2 *pairs, const int *npairs, int nleaves,
-                                 int stride, int max_pairs, int m0, int m1, int c0, int c1, unsigned *umax,
-                                 cudaStream_t s);
 // Applies the moves to an int vector (the running row permutation).
 cudaError_t launch_apply_moves_vec(int *v, const int2 *pairs, const int *npairs, int max_pairs,
                                    cudaStream_t s);
@@ -160,11 +149,6 @@ template <typename T> size_t trsv_sync_bytes(int n);  // counters of one solve (
 template <typename T>
 cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
                                   bool lower_unit = true, bool upper_unit = false);
-// The same for the diagonal blocks [b0, b1) only (blocks of the n x n
-// factors' BI; Linv/Uinv/W are the full buffers); tmp as above.
-template <typename T>
-cudaError_t launch_build_inverses_range(int n, int b0, int b1, const T *W, long ldw, T *Linv, T *Uinv, T *tmp,
-                                        cudaStream_t s, bool lower_unit = true, bool upper_unit = false);
 // Lower solve: Y[:,c] = L^{-1} (P r_c) / s_c with r FP64 col-major (ldr), perm
 // (nullptr: identity)
 // the row permutation, s_c = 2^ceil(log2 rnorm[c]).  acc: n*nrhs scratch of T;

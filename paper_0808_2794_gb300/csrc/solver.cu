@@ -174,7 +174,6 @@ extern "C" void mp_default_opts(mp_opts *o) {
     o->allow_fallback = 1;
     o->nb_outer = 0;
     o->nb_inner = 0;
-    o->lookahead = -1;
 }
 
 extern "C" int mp_factor_ld(int n) { return std::max(32, (n + 31) / 32 * 32); }
@@ -182,10 +181,6 @@ extern "C" int mp_factor_ld(int n) { return std::max(32, (n + 31) / 32 * 32); }
 namespace {
 
 constexpr int kMaxRhs = 8;
-// Per-leaf move storage of the look-ahead: kLaMaxLeaves leaves (an outer
-// panel of at most 1024 columns in leaves of at least 8) of kLaPairs moves.
-constexpr int kLaMaxLeaves = 128;
-constexpr int kLaPairs = 64;
 
 // Status block in device memory, read back by the host once per iteration.
 struct StatusBlock {
@@ -218,8 +213,7 @@ int outer_nb(int n, const mp_opts &o) {
 // ---------------------------------------------------------------------------
 struct Layout {
     size_t status, rowsum, W, perm, ipiv, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, R, Y, Z,
-        part, tc, linv, gV, gZ, gsm, la_pairs, la_npairs, tc_wide, total;
-    bool la;  // the outer look-ahead's buffers are carved
+        part, tc, linv, gV, gZ, gsm, total;
     size_t W_bytes;
     int ldw, nblk, ksplit, nb;
 };
@@ -233,13 +227,6 @@ size_t carve(size_t &off, size_t bytes) {
 
 // Room for FP64 factors is needed by the fallback and by the plain FP64 solve.
 bool fp64_space_of(const mp_opts &o) { return o.allow_fallback != 0 || o.prec == MP_PREC_FP64; }
-
-// The outer look-ahead runs on the tensor-core rungs (the trailing update a
-// separate persistent kernel that can share the GPU with the panel chain).
-bool lookahead_on(int n, const mp_opts &o) {
-    const bool tc = o.prec != MP_PREC_FP32 && o.prec != MP_PREC_FP64;
-    return tc && (o.lookahead == 1 || (o.lookahead == -1 && n >= 4096));
-}
 
 // fp64_space: room for the FP64 fallback (W, inverses, vectors sized for double)
 Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym = false) {
@@ -258,8 +245,7 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.perm = carve(off, sizeof(int) * (size_t)n);
     L.ipiv = carve(off, sizeof(int) * (size_t)n);
     L.pairs = carve(off, sizeof(int2) * ((size_t)2 * (size_t)std::max(n, L.nb) + 128));  // + two leaves' moves
-    L.npairs = carve(off, sizeof(int) * 32);  // [0], [1]: two leaves' move counts, [2]: max |U12|, [4..20): tickets,
-                                              // [21], [22]: the look-ahead's max |U12|
+    L.npairs = carve(off, sizeof(int) * 32);  // [0], [1]: two leaves' move counts, [2]: max |U12|, [4..20): tickets
     L.map = carve(off, sizeof(int) * (size_t)n);
     const size_t inv_bytes = std::max(trsv_inverse_bytes<float>(n), fp64_space ? trsv_inverse_bytes<double>(n) : 0);
     L.Linv = carve(off, inv_bytes);
@@ -282,11 +268,6 @@ Layout make_layout(int n, int nrhs, const mp_opts &o, bool fp64_space, bool sym 
     L.gV = carve(off, m ? sizeof(double) * (size_t)n * (m + 1) : 0);
     L.gZ = carve(off, sizeof(double) * (size_t)n * m);
     L.gsm = carve(off, m ? sizeof(double) * (3 * m + 8) : 0);
-    L.la = !sym && lookahead_on(n, o);
-    L.la_pairs = carve(off, L.la ? sizeof(int2) * 2 * kLaMaxLeaves * kLaPairs : 0);
-    L.la_npairs = carve(off, L.la ? sizeof(int) * 2 * kLaMaxLeaves : 0);
-    L.tc_wide = carve(off, L.la ? std::max(tc_workspace_bytes(n, L.nb, o.prec), tc_workspace_bytes(n, L.nb, MP_PREC_FP16X3))
-                                : 0);
     L.total = align_up(off, 256);
     return L;
 }
@@ -324,15 +305,6 @@ struct FactorCtx {
     int prec;
     void *tc;
     T *linv;  // inverse of the last leaf's L11 (panel_base_width^2 elements)
-    // diagonal-block inverses for the triangular solves (trsv_inverse_block
-    // blocks), built during the factorization by the look-ahead
-    T *Linv = nullptr, *Uinv = nullptr, *invtmp = nullptr;
-    bool inverses_built = false;
-    // outer look-ahead (getrf_blocked_la): every leaf's row moves of the two
-    // most recent outer panels, and the concurrent stream's tensor-core scratch
-    int2 *la_pairs = nullptr;
-    int *la_npairs = nullptr;
-    void *tc_wide = nullptr;
 };
 
 #define CU(expr)                                      \
@@ -372,7 +344,6 @@ cudaError_t trsm_rec(FactorCtx<T> &c, int m, int N, const T *L, long ldl, T *B, 
 // update (created once).
 struct PanelStreams {
     cudaStream_t hi = nullptr, lo = nullptr;
-    cudaStream_t wide = nullptr;  // low priority: the look-ahead's deferred trailing work
 };
 PanelStreams panel_streams() {
     static std::mutex mu;
@@ -385,8 +356,7 @@ PanelStreams panel_streams() {
         int lo_pri = 0, hi_pri = 0;
         if (cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri) != cudaSuccess ||
             cudaStreamCreateWithPriority(&p.hi, cudaStreamNonBlocking, hi_pri) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&p.lo, cudaStreamNonBlocking, lo_pri) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&p.wide, cudaStreamNonBlocking, lo_pri) != cudaSuccess)
+            cudaStreamCreateWithPriority(&p.lo, cudaStreamNonBlocking, lo_pri) != cudaSuccess)
             p = PanelStreams{};
     }
     return p;
@@ -406,15 +376,8 @@ PanelStreams panel_streams() {
 // that the next panel kernel always finds a free cluster slot beside it.  A
 // panel kernel waits for the bulk launch of two leaves before.  L11^{-1} and
 // the moves of two consecutive leaves live in alternating buffers.
-// la_par >= 0: the outer look-ahead's form.  The leaves' moves are kept in
-// the per-leaf buffers of parity la_par (*nleaves of them), and the leaf
-// steps touch the outer panel's own columns only: the row exchange over the
-// other columns and U12 are left to the caller.  la_bulk_clusters > 0 caps
-// the bulk launches' clusters.
 template <typename T>
-cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsigned **u12_max, int la_par = -1,
-                        int *nleaves = nullptr, int la_bulk_clusters = 0) {
-    const bool la = la_par >= 0 && c.la_pairs && c.la_npairs;
+cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsigned **u12_max) {
     T *W = c.W;
     const long ld = c.ld;
     unsigned *ticket = reinterpret_cast<unsigned *>(c.npairs + 4);  // one per 128-column chunk
@@ -440,7 +403,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
     }
     const int tc0 = k0 + ncols, tc1 = c.n;  // the trailing columns
     // max |U12| for the scaled tensor-core rungs, raised as U12 is formed
-    unsigned *umax = (two && !la && sizeof(T) == 4 && c.prec != MP_PREC_FP32 && tc1 > tc0)
+    unsigned *umax = (two && sizeof(T) == 4 && c.prec != MP_PREC_FP32 && tc1 > tc0)
                          ? reinterpret_cast<unsigned *>(c.npairs + 2)
                          : nullptr;
     // zeroed on the bulk stream, ahead of every launch that raises it
@@ -457,12 +420,8 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
         // moves (two buffers)
         T *X = c.linv + (leaf % 3) * 1024;
         T *Xprev = c.linv + ((leaf + 2) % 3) * 1024;
-        if (la && leaf >= kLaMaxLeaves) {
-            err = cudaErrorInvalidValue;
-            break;
-        }
-        int2 *pairs = la ? c.la_pairs + ((size_t)la_par * kLaMaxLeaves + leaf) * kLaPairs : c.pairs + (leaf & 1) * 64;
-        int *npairs = la ? c.la_npairs + la_par * kLaMaxLeaves + leaf : c.npairs + (leaf & 1);
+        int2 *pairs = c.pairs + (leaf & 1) * 64;
+        int *npairs = c.npairs + (leaf & 1);
         if (!two) {
             {
                 MpProfScope ps(MP_KC_PANEL, (double)m * kb * kb - (double)kb * kb * kb / 3.0, hi);
@@ -472,10 +431,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
             }
             {
                 MpProfScope ps(MP_KC_ROWMOVES, 4.0 * kb * (double)(c.n - kb) * sizeof(T), hi);
-                // look-ahead: the outer panel's own columns only
-                if (!chk(launch_apply_moves<T>(W, ld, pairs, npairs, 2 * kb, la ? k0 : 0, k, k + kb,
-                                               la ? k0 + ncols : c.n, c.perm, hi)))
-                    break;
+                if (!chk(launch_apply_moves<T>(W, ld, pairs, npairs, 2 * kb, 0, k, k + kb, c.n, c.perm, hi))) break;
             }
             if (N > 0) {
                 MpProfScope ps(MP_KC_PANELGEMM, (double)kb * kb * N + 2.0 * (m - kb) * N * kb, hi);
@@ -489,9 +445,8 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
             PanelPrev<T> pv;
             if (leaf >= 1) {
                 pv.X = Xprev;
-                pv.pairs = la ? c.la_pairs + ((size_t)la_par * kLaMaxLeaves + leaf - 1) * kLaPairs
-                              : c.pairs + ((leaf - 1) & 1) * 64;
-                pv.npairs = la ? c.la_npairs + la_par * kLaMaxLeaves + leaf - 1 : c.npairs + ((leaf - 1) & 1);
+                pv.pairs = c.pairs + ((leaf - 1) & 1) * 64;
+                pv.npairs = c.npairs + ((leaf - 1) & 1);
                 pv.xs = xs_prev;
                 pv.kb = kb_prev;
             }
@@ -509,8 +464,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
             // clusters of the next panel's size, leaving one such cluster free
             const int kb_next = N > 0 ? std::min(panel_base_width<T>(m - kb), N) : 0;
             const int cl = panel_cluster_size<T>(std::max(1, m - kb));
-            const int G = la && la_bulk_clusters > 0 ? std::min(la_bulk_clusters, leaf_update_rest_clusters<T>(cl))
-                                                     : leaf_update_rest_clusters<T>(cl);
+            const int G = leaf_update_rest_clusters<T>(cl);
             LeafRestArgs<T> ra;
             ra.W = W;
             ra.ld = ld;
@@ -524,12 +478,11 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
             ra.tickets = ticket + 8;
             ra.pairs = pairs;
             ra.npairs = npairs;
-            ra.mc0 = la ? k0 : 0;
             ra.mc1 = k;
             ra.mc2 = tc0;
-            ra.mc3 = la ? tc0 : tc1;
+            ra.mc3 = tc1;
             ra.perm = c.perm;
-            if (!la && leaf >= 1 && tc1 > tc0) {
+            if (leaf >= 1 && tc1 > tc0) {
                 ra.Xp = Xprev;
                 ra.xps = xs_prev;
                 ra.kp = k_prev;
@@ -551,8 +504,7 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
         k_prev = k;
         k += kb;
     }
-    if (nleaves) *nleaves = leaf;
-    if (two && !la && err == cudaSuccess && tc1 > tc0) {
+    if (two && err == cudaSuccess && tc1 > tc0) {
         // the last leaf's U rows over the trailing columns
         LeafRestArgs<T> ra;
         ra.W = W;
@@ -579,190 +531,9 @@ cudaError_t getrf_panel(FactorCtx<T> &c, int k0, int ncols, bool *u12_done, unsi
         cudaEventDestroy(ev_chain);
         cudaEventDestroy(ev_rest[0]);
         cudaEventDestroy(ev_rest[1]);
-        *u12_done = !la && err == cudaSuccess && tc1 > tc0;
+        *u12_done = err == cudaSuccess && tc1 > tc0;
         if (u12_max) *u12_max = *u12_done ? umax : nullptr;
     }
-    return err;
-}
-
-// The diagonal blocks of L and U that the triangular solves invert (rows
-// and columns [b BI, (b+1) BI)) are final once the outer panels have passed
-// their last column and those panels' row moves have reached every column:
-// later pivots exchange rows below them only, and the trailing updates write
-// below and right of them.  With the outer look-ahead each block is inverted
-// on the look-ahead's low-priority stream as soon as that holds, in the
-// shadow of the next panels' factorization; only the last block's inversion
-// follows the factorization.  (On a stream of its own beside the plain
-// blocked form, the inversions delayed the panel chain by more than they
-// saved, so that form inverts after the factorization.)
-template <typename T>
-struct InverseSide {
-    cudaStream_t side = nullptr, user = nullptr;
-    cudaEvent_t ev = nullptr;
-    int next = 0, nbi = 0, BI = 0;
-
-    bool begin(FactorCtx<T> &c, cudaStream_t stream) {
-        if (!c.Linv || !c.Uinv || !c.invtmp || !stream) return false;
-        side = stream;
-        user = c.s;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-            ev = nullptr;
-            return false;
-        }
-        BI = trsv_inverse_block<T>(c.n);
-        nbi = (c.n + BI - 1) / BI;
-        return true;
-    }
-    // rows and columns [0, done) of the factors are final once the work
-    // queued so far on the side stream has run
-    cudaError_t advance(FactorCtx<T> &c, int done) {
-        if (!ev) return cudaSuccess;
-        const int b1 = done >= c.n ? nbi : done / BI;
-        if (b1 <= next) return cudaSuccess;
-        CU(launch_build_inverses_range<T>(c.n, next, b1, c.W, c.ld, c.Linv, c.Uinv, c.invtmp, side));
-        next = b1;
-        return cudaSuccess;
-    }
-    // the caller's stream waits for the inversions
-    cudaError_t finish(FactorCtx<T> &c) {
-        if (!ev) return cudaSuccess;
-        cudaError_t e = cudaEventRecord(ev, side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s, ev, 0);
-        cudaEventDestroy(ev);
-        ev = nullptr;
-        if (e == cudaSuccess && next == nbi) c.inverses_built = true;
-        return e;
-    }
-    ~InverseSide() {
-        if (ev) {  // an error path: order the side stream before the caller's anyway
-            cudaEventRecord(ev, side);
-            cudaStreamWaitEvent(user, ev, 0);
-            cudaEventDestroy(ev);
-        }
-    }
-};
-
-// How the GPU's cluster slots of one size are shared while R_p runs beside
-// F_{p+1}: one for the panel kernel, a third of the rest for the leaf steps'
-// bulk launches (which touch the panel's own columns only), the others for
-// the update kernel.
-struct LaSplit {
-    int cluster, bulk, update;
-};
-template <typename T>
-LaSplit la_split(int prec, int cl) {
-    const int tot = std::min(leaf_update_rest_clusters<T>(cl) + 1, tc_max_clusters(prec, cl));
-    LaSplit sp;
-    sp.cluster = cl;
-    sp.bulk = std::max(1, (tot - 1) / 3);
-    sp.update = std::max(1, tot - 1 - sp.bulk);
-    return sp;
-}
-
-// Blocked LU with outer look-ahead (tensor-core rungs).  Outer panel p
-// (columns [k, k + nbk)) is factored touching its own columns only (F_p);
-// then, on the caller's stream, the next panel's columns receive panel p's
-// row moves, U12 = L11^{-1} A12 and the update A22 -= L21 U12 (N_p), after
-// which F_{p+1} starts at once.  The same three steps for every column right
-// of the next panel, and the moves over the columns left of panel p, run on a
-// low-priority stream (R_p) concurrently with F_{p+1}: the update kernel then
-// runs as whole thread-block clusters beside the panel's clusters.  R_p
-// updates the columns of panel p + 2 first (N_{p+1} waits for them), then
-// the rest.  Every step's arithmetic is that of the plain blocked form, with
-// U12 formed by blocked substitution in FP32 FMAs.
-template <typename T>
-cudaError_t getrf_blocked_la(FactorCtx<T> &c, int nb) {
-    const int n = c.n;
-    T *W = c.W;
-    const long ld = c.ld;
-    const cudaStream_t C = c.s, Wd = panel_streams().wide;
-    constexpr int KBMAX = sizeof(T) == 4 ? 24 : 8;
-    CU(cudaMemsetAsync(c.npairs + 4, 0, 16 * sizeof(int), C));  // the leaf-update tickets (two sets)
-    cudaEvent_t evF = nullptr, evSlice[2] = {nullptr, nullptr}, evEnd = nullptr;
-    cudaError_t err = cudaSuccess;
-    auto chk = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; return err == cudaSuccess; };
-    for (cudaEvent_t *e : {&evF, &evSlice[0], &evSlice[1], &evEnd})
-        chk(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    InverseSide<T> inv;
-    if (err == cudaSuccess) inv.begin(c, Wd);
-    // the caller's stream and the wide stream start from the same point
-    if (chk(cudaEventRecord(evF, C))) chk(cudaStreamWaitEvent(Wd, evF, 0));
-    // max |U12| of the next panel's columns and of the columns right of it
-    unsigned *umax_n = reinterpret_cast<unsigned *>(c.npairs + 21), *umax_w = reinterpret_cast<unsigned *>(c.npairs + 22);
-    for (int p = 0, k = 0; k < n && err == cudaSuccess; ++p, k += nb) {
-        const int nbk = std::min(nb, n - k), par = p & 1, rest = n - k - nbk;
-        const int nw = std::min(nb, rest);       // the next panel's columns
-        const int ns = std::min(nb, rest - nw);  // the panel after it
-        // R_p runs beside F_{p+1}: its update kernel as whole clusters of
-        // F_{p+1}'s cluster size, the leaf steps' bulk in some of the others
-        const LaSplit sp_next = la_split<T>(c.prec, panel_cluster_size<T>(std::max(1, n - k - nbk)));
-        const LaSplit sp_own = la_split<T>(c.prec, panel_cluster_size<T>(std::max(1, n - k)));
-        TcShape shape;
-        shape.cluster = sp_next.cluster;
-        shape.clusters = sp_next.update;
-        bool u12_done = false;
-        int nl = 0;
-        if (!chk(getrf_panel<T>(c, k, nbk, &u12_done, nullptr, par, &nl, sp_own.bulk))) break;
-        if (!chk(cudaEventRecord(evF, C))) break;
-        const int2 *pp = c.la_pairs + (size_t)par * kLaMaxLeaves * kLaPairs;
-        const int *np = c.la_npairs + par * kLaMaxLeaves;
-        const T *L21 = W + (long)(k + nbk) * ld + k;
-        const long j0 = k + nbk;
-        if (rest > 0) {
-            // N_p: the next panel's columns, on the caller's stream
-            MpProfScope pl(MP_KC_LOOKAHEAD, 0.0, C);
-            if (p >= 1 && !chk(cudaStreamWaitEvent(C, evSlice[par ^ 1], 0))) break;
-            {
-                MpProfScope ps(MP_KC_TRSM, (double)nbk * nbk * nw, C);
-                if (!chk(cudaMemsetAsync(umax_n, 0, sizeof(unsigned), C)) ||
-                    !chk(launch_la_moves_trsm<T>(W, ld, k, nbk, pp, np, nl, kLaPairs, 2 * KBMAX, 0, 0, (int)j0,
-                                                 (int)j0 + nw, umax_n, C)))
-                    break;
-            }
-            {
-                MpProfScope ps(MP_KC_UPDATE, 2.0 * rest * nw * nbk, C);
-                if (!chk(tc_trailing_update(c.prec, rest, nw, nbk, reinterpret_cast<const float *>(L21), ld,
-                                            reinterpret_cast<const float *>(W + (long)k * ld + j0), ld,
-                                            reinterpret_cast<float *>(W + j0 * ld + j0), ld, c.tc, c.st, C, umax_n)))
-                    break;
-            }
-        }
-        // R_p on the wide stream, after F_p: the moves over the columns left
-        // of panel p and right of the next one, then U12 and the update there
-        if (!chk(cudaStreamWaitEvent(Wd, evF, 0))) break;
-        const int w0 = k + nbk + nw;  // first column right of the next panel
-        {
-            MpProfScope ps(MP_KC_TRSM, (double)nbk * nbk * (n - w0), Wd);
-            if (!chk(cudaMemsetAsync(umax_w, 0, sizeof(unsigned), Wd)) ||
-                !chk(launch_la_moves_trsm<T>(W, ld, k, nbk, pp, np, nl, kLaPairs, 2 * KBMAX, 0, k, w0, n, umax_w,
-                                             Wd)))
-                break;
-        }
-        if (n > w0) {
-            MpProfScope ps(MP_KC_UPDATE, 2.0 * rest * (n - w0) * nbk, Wd);
-            // all trailing rows [j0, n); the columns of panel p + 2 first
-            // (N_{p+1} waits for them), then the rest
-            for (int part = 0; part < 2; ++part) {
-                const int c0 = part ? w0 + ns : w0, nc = part ? n - w0 - ns : ns;
-                if (nc > 0 && !chk(tc_trailing_update(c.prec, rest, nc, nbk, reinterpret_cast<const float *>(L21), ld,
-                                                      reinterpret_cast<const float *>(W + (long)k * ld + c0), ld,
-                                                      reinterpret_cast<float *>(W + j0 * ld + c0), ld, c.tc_wide, c.st,
-                                                      Wd, umax_w, &shape)))
-                    break;
-                if (part == 0 && !chk(cudaEventRecord(evSlice[par], Wd))) break;
-            }
-            if (err != cudaSuccess) break;
-        } else if (!chk(cudaEventRecord(evSlice[par], Wd))) {
-            break;
-        }
-        chk(inv.advance(c, k + nbk));
-    }
-    // the caller's stream follows the wide stream (on an error path too, so
-    // that no work on the workspace outlives the call)
-    if (evEnd && cudaEventRecord(evEnd, Wd) == cudaSuccess) chk(cudaStreamWaitEvent(C, evEnd, 0));
-    if (err == cudaSuccess) chk(inv.finish(c));
-    for (cudaEvent_t e : {evF, evSlice[0], evSlice[1], evEnd})
-        if (e) cudaEventDestroy(e);
     return err;
 }
 
@@ -771,8 +542,6 @@ cudaError_t getrf_blocked_la(FactorCtx<T> &c, int nb) {
 // at precision prec.
 template <typename T>
 cudaError_t getrf_blocked(FactorCtx<T> &c, int nb) {
-    if (sizeof(T) == 4 && c.la_pairs && c.la_npairs && c.tc_wide && c.prec != MP_PREC_FP32 && panel_streams().wide)
-        return getrf_blocked_la<T>(c, nb);
     const int n = c.n;
     T *W = c.W;
     const long ld = c.ld;
@@ -980,17 +749,9 @@ int factor(Solve &S, int prec, int nb, int *info_out, uint32_t *flags_out) {
         MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
                                              at<T>(S.work, L.invtmp), S.s, false));
     } else {
-        c.Linv = at<T>(S.work, L.Linv);
-        c.Uinv = at<T>(S.work, L.Uinv);
-        c.invtmp = at<T>(S.work, L.invtmp);
-        if (L.la) {  // sized for every tensor-core rung
-            c.la_pairs = at<int2>(S.work, L.la_pairs);
-            c.la_npairs = at<int>(S.work, L.la_npairs);
-            c.tc_wide = at<void>(S.work, L.tc_wide);
-        }
         MP_CUDA_TRY(getrf_blocked<T>(c, nb));
-        if (!c.inverses_built)
-            MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, c.Linv, c.Uinv, c.invtmp, S.s));
+        MP_CUDA_TRY(launch_build_inverses<T>(S.n, W, L.ldw, at<T>(S.work, L.Linv), at<T>(S.work, L.Uinv),
+                                             at<T>(S.work, L.invtmp), S.s));
     }
     StatusBlock h;
     int e = read_status(S, h);
@@ -1251,7 +1012,6 @@ int validate_opts(const mp_opts &o) {
     if (o.prec < MP_PREC_FP32 || o.prec > MP_PREC_FP64) return 1;
     if (o.itermax < 0 || !(o.tol > 0.0) || o.stall_ratio <= 0.0) return 1;
     if (o.refine < MP_REFINE_CLASSICAL || o.refine > MP_REFINE_AUTO) return 1;
-    if (o.lookahead < -1 || o.lookahead > 1) return 1;
     if (o.refine != MP_REFINE_CLASSICAL &&
         (o.gmres_restart < 1 || o.gmres_restart > 128 || !(o.gmres_tol > 0.0) || !(o.gmres_tol < 1.0)))
         return 1;
@@ -1642,12 +1402,10 @@ extern "C" int mp_gesv_host(int n, int nrhs, const double *hA, int lda, const do
 // ---------------------------------------------------------------------------
 namespace {
 struct StepLayout {
-    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, Y, Z, part, tc, linv, la_pairs,
-        la_npairs, tc_wide, total;
+    size_t status, rowsum, perm, pairs, npairs, map, Linv, Uinv, invtmp, acc, bar, Y, Z, part, tc, linv, total;
     int nblk, ksplit;
-    bool la;
 };
-StepLayout step_layout(int n, int nrhs, int nb, int prec, bool la = false) {
+StepLayout step_layout(int n, int nrhs, int nb, int prec) {
     StepLayout L{};
     L.nblk = (n + 127) / 128;
     L.ksplit = residual_ksplit(std::max(n, 1), std::max(nrhs, 1));
@@ -1671,11 +1429,6 @@ StepLayout step_layout(int n, int nrhs, int nb, int prec, bool la = false) {
                                            : std::max(tc_workspace_bytes(n, nb, prec),
                                                       tc_workspace_bytes(n, nb, MP_PREC_FP16X3)));
     L.linv = carve(off, 3 * 1024 * sizeof(double));
-    L.la = la && prec != MP_PREC_FP32;
-    L.la_pairs = carve(off, L.la ? sizeof(int2) * 2 * kLaMaxLeaves * kLaPairs : 0);
-    L.la_npairs = carve(off, L.la ? sizeof(int) * 2 * kLaMaxLeaves : 0);
-    L.tc_wide = carve(off, L.la ? std::max(tc_workspace_bytes(n, nb, prec), tc_workspace_bytes(n, nb, MP_PREC_FP16X3))
-                                : 0);
     L.total = align_up(off, 256);
     return L;
 }
@@ -1685,7 +1438,7 @@ extern "C" size_t mp_getrf_workspace_bytes(int n, const mp_opts *opts) {
     mp_opts o;
     if (opts) o = *opts; else mp_default_opts(&o);
     if (n < 0) return 0;
-    return step_layout(n, 1, outer_nb(n, o), o.prec, lookahead_on(n, o)).total;
+    return step_layout(n, 1, outer_nb(n, o), o.prec).total;
 }
 extern "C" size_t mp_getrs_workspace_bytes(int n, int nrhs) {
     if (n < 0 || nrhs < 0) return 0;
@@ -1731,7 +1484,7 @@ extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp
     if (n > 0 && !dipiv) return mp_arg_fail(4, "ipiv is NULL");
     if (validate_opts(o) || o.prec == MP_PREC_FP64) return mp_arg_fail(5, "invalid options");
     const int nb = outer_nb(n, o);
-    StepLayout L = step_layout(n, 1, nb, o.prec, lookahead_on(n, o));
+    StepLayout L = step_layout(n, 1, nb, o.prec);
     if (!work) return mp_arg_fail(6, "workspace is NULL");
     if (work_bytes < L.total) return mp_arg_fail(7, "workspace too small");
     if (info) *info = 0;
@@ -1745,11 +1498,6 @@ extern "C" int mp_getrf_lowp(int n, float *dW, int ldw, int32_t *dipiv, const mp
     FactorCtx<float> c{dW, (long)ldw, n, dipiv, at<int>(work, L.perm), at<int2>(work, L.pairs),
                        at<int>(work, L.npairs), at<int>(work, L.map), &sb->st, s, o.prec, at<void>(work, L.tc),
                        at<float>(work, L.linv)};
-    if (L.la) {
-        c.la_pairs = at<int2>(work, L.la_pairs);
-        c.la_npairs = at<int>(work, L.la_npairs);
-        c.tc_wide = at<void>(work, L.tc_wide);
-    }
     MP_CUDA_TRY(getrf_blocked<float>(c, nb));
     StatusBlock h;
     MP_CUDA_TRY(cudaMemcpyAsync(&h, sb, sizeof h, cudaMemcpyDeviceToHost, s));

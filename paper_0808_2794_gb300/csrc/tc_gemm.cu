@@ -573,7 +573,7 @@ TcWs carve_ws(void *ws, int M, int N, int Kpad, int split, int esz) {
 template <typename H, uint32_t FMT, int SPLIT>
 cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U12, long ldu, float *A22, long lda,
                 void *ws, MpDevStatus *st, cudaStream_t s, bool nt = false, int lower = 0,
-                const unsigned *umax_pre = nullptr, const TcShape *shape = nullptr) {
+                const unsigned *umax_pre = nullptr) {
     constexpr int BKE = bk_elems<FMT>();
     constexpr bool SCALED = scaled<FMT, SPLIT>();
     const int Kpad = (K + BKE - 1) / BKE * BKE;
@@ -658,33 +658,6 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
     if (e != cudaSuccess) return e;
     const int ntiles = ((M + TILE_I - 1) / TILE_I) * ((N + TILE_J - 1) / TILE_J);
     const int grid = std::min(ntiles, num_sms());
-    const bool shaped = shape && shape->clusters > 0 && shape->cluster >= 1 && shape->cluster <= 16;
-    if (shaped && shape->cluster > 8) {
-        e = mp_func_attr_once(reinterpret_cast<const void *>(kern), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    auto launch = [&](int kb_count, const BlockScales &bsv) -> cudaError_t {
-        mp_note_launch();
-        if (!shaped) {
-            kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, kb_count, (int)a_lo, (int)b_lo,
-                                                 w.scales + 2, st, lower, bsv);
-            return cudaGetLastError();
-        }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3((unsigned)(shape->clusters * shape->cluster), 1, 1);
-        cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)shape->cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, A22, lda, M, N, kb_count, (int)a_lo, (int)b_lo,
-                                  (const float *)(w.scales + 2), st, lower, bsv);
-    };
     if (FMT == 2) {
         // one launch per K-block: each block's products carry their own scales
         BlockScales bs;
@@ -697,36 +670,16 @@ cudaError_t run(int M, int N, int K, const float *L21, long ldl, const float *U1
         bs.nrb = blocks128(M);
         for (int kb = 0; kb < KBk; ++kb) {
             bs.k_first = kb;
-            if ((e = launch(1, bs)) != cudaSuccess) return e;
+            mp_note_launch();
+            kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, 1, (int)a_lo, (int)b_lo, w.scales + 2, st,
+                                                 lower, bs);
         }
-        return cudaSuccess;
+        return cudaGetLastError();
     }
-    return launch(KBk, BlockScales{});
-}
-
-template <uint32_t FMT, int SPLIT>
-int max_clusters_of(int cluster) {
-    auto kern = tc_update_kernel<FMT, SPLIT>;
-    constexpr size_t smem = smem_bytes<SPLIT>();
-    if (mp_smem_attr(kern, smem) != cudaSuccess) return 0;
-    if (cluster > 8 && mp_func_attr_once(reinterpret_cast<const void *>(kern),
-                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        return 0;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)cluster, 1, 1);
-    cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, reinterpret_cast<const void *>(kern), &cfg) != cudaSuccess) nc = 0;
-    cudaGetLastError();
-    return nc;
+    mp_note_launch();
+    kern<<<grid, NUM_THREADS, smem, s>>>(mapA, mapB, A22, lda, M, N, KBk, (int)a_lo, (int)b_lo, w.scales + 2, st,
+                                         lower, BlockScales{});
+    return cudaGetLastError();
 }
 
 // Timeout path of the tensor-core kernels' bounded mbarrier wait, for the
@@ -768,27 +721,17 @@ size_t tc_workspace_bytes(int n, int nb, int prec) {
 
 cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, long ldl, const float *U12,
                                long ldu, float *A22, long lda, void *ws, MpDevStatus *st, cudaStream_t s,
-                               const unsigned *umax_pre, const TcShape *shape) {
+                               const unsigned *umax_pre) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (prec == MP_PREC_BF16)
-        return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre, shape);
+        return run<__nv_bfloat16, 1, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
     if (prec == MP_PREC_FP16)
-        return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre, shape);
+        return run<__half, 0, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
     if (prec == MP_PREC_FP16X3)
-        return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre, shape);
+        return run<__half, 0, 2>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
     if (prec == MP_PREC_E4M3)
-        return run<__nv_fp8_e4m3, 2, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre,
-                                        shape);
+        return run<__nv_fp8_e4m3, 2, 1>(M, N, K, L21, ldl, U12, ldu, A22, lda, ws, st, s, false, 0, umax_pre);
     return cudaErrorInvalidValue;
-}
-
-int tc_max_clusters(int prec, int cluster) {
-    if (cluster < 1 || cluster > 16) return 0;
-    if (prec == MP_PREC_BF16) return max_clusters_of<1, 1>(cluster);
-    if (prec == MP_PREC_FP16) return max_clusters_of<0, 1>(cluster);
-    if (prec == MP_PREC_FP16X3) return max_clusters_of<0, 2>(cluster);
-    if (prec == MP_PREC_E4M3) return max_clusters_of<2, 1>(cluster);
-    return 0;
 }
 
 cudaError_t tc_update_nt(int prec, int M, int N, int K, const float *A, long lda, const float *B, long ldb,

@@ -12,20 +12,9 @@ size_t tc_workspace_bytes(int n, int nb, int prec);
 // umax_pre (optional, device): max |U12| as the uint bits of a non-negative
 // float (NaN counted as infinite), taken while U12 was formed; the scaled
 // rungs then skip their own pass over U12.
-// shape (optional): the GEMM kernel runs as `clusters` thread-block clusters
-// of `cluster` CTAs (one CTA per SM) instead of one CTA on every SM, so that
-// it holds whole cluster slots and leaves the rest of the GPU to concurrent
-// clustered kernels; clusters = 0 keeps the default.
-struct TcShape {
-    int clusters = 0, cluster = 1;
-};
 cudaError_t tc_trailing_update(int prec, int M, int N, int K, const float *L21, long ldl,
                                const float *U12, long ldu, float *A22, long lda, void *ws,
-                               MpDevStatus *st, cudaStream_t s, const unsigned *umax_pre = nullptr,
-                               const TcShape *shape = nullptr);
-// Clusters of `cluster` CTAs of the update kernel (rung prec) that fit on the
-// device at once (0 when none or on error).
-int tc_max_clusters(int prec, int cluster);
+                               MpDevStatus *st, cudaStream_t s, const unsigned *umax_pre = nullptr);
 
 // C[M x N] -= fl_p(A[M x K]) fl_p(B[N x K])^T (B given row-major N x K, as for
 // the symmetric update A22 -= L21 L21^T); lower != 0: only the tiles of C on

@@ -452,15 +452,13 @@ template size_t trsv_tmp_bytes<float>(int);
 template size_t trsv_tmp_bytes<double>(int);
 
 // Builds inv(L_bb) and inv(U_bb) for the BI x BI diagonal blocks of the
-// row-major n x n factors in W, BI dividing the blocks from the top left (the
-// last one may be partial).  Every block is independent, so the caller may
-// pass a range of blocks as a smaller matrix: W and the inverse buffers
-// offset to the range's first block, n the rows of the range.
+// row-major factors in W.  tmp holds trsv_tmp_bytes<T>(n).
 template <typename T>
-cudaError_t build_inverses_impl(int n, int BI, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
-                                bool lower_unit, bool upper_unit) {
+cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
+                                  bool lower_unit, bool upper_unit) {
     if (n <= 0) return cudaSuccess;
     constexpr int BS = base_bs<T>();
+    const int BI = trsv_inverse_block<T>(n);
     const int nbi = (n + BI - 1) / BI;
     const size_t bytes = (size_t)nbi * BI * BI * sizeof(T);
     cudaError_t e = cudaMemsetAsync(Linv, 0, bytes, s);
@@ -529,28 +527,6 @@ cudaError_t build_inverses_impl(int n, int BI, const T *W, long ldw, T *Linv, T 
     }
     return cudaSuccess;
 }
-
-// tmp holds trsv_tmp_bytes<T>(n).
-template <typename T>
-cudaError_t launch_build_inverses(int n, const T *W, long ldw, T *Linv, T *Uinv, T *tmp, cudaStream_t s,
-                                  bool lower_unit, bool upper_unit) {
-    return build_inverses_impl<T>(n, trsv_inverse_block<T>(n), W, ldw, Linv, Uinv, tmp, s, lower_unit, upper_unit);
-}
-
-template <typename T>
-cudaError_t launch_build_inverses_range(int n, int b0, int b1, const T *W, long ldw, T *Linv, T *Uinv, T *tmp,
-                                        cudaStream_t s, bool lower_unit, bool upper_unit) {
-    const int BI = trsv_inverse_block<T>(n);
-    const long r0 = (long)b0 * BI, r1 = std::min<long>(n, (long)b1 * BI);
-    if (b0 < 0 || r1 <= r0) return cudaSuccess;
-    const long off = r0 * BI;  // block b0 of the inverse buffers
-    return build_inverses_impl<T>((int)(r1 - r0), BI, W + r0 * ldw + r0, ldw, Linv + off, Uinv + off, tmp, s,
-                                  lower_unit, upper_unit);
-}
-template cudaError_t launch_build_inverses_range<float>(int, int, int, const float *, long, float *, float *,
-                                                        float *, cudaStream_t, bool, bool);
-template cudaError_t launch_build_inverses_range<double>(int, int, int, const double *, long, double *, double *,
-                                                         double *, cudaStream_t, bool, bool);
 template cudaError_t launch_build_inverses<float>(int, const float *, long, float *, float *, float *, cudaStream_t,
                                                   bool, bool);
 template cudaError_t launch_build_inverses<double>(int, const double *, long, double *, double *, double *,

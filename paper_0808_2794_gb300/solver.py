@@ -33,7 +33,7 @@ class mp_opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("stall_ratio", ctypes.c_double),
                 ("allow_fallback", ctypes.c_int), ("nb_outer", ctypes.c_int),
-                ("nb_inner", ctypes.c_int), ("lookahead", ctypes.c_int)]
+                ("nb_inner", ctypes.c_int)]
 
 
 class mp_stats(ctypes.Structure):
@@ -130,9 +130,7 @@ _SIGS = {
     "mp_launch_count": (ctypes.c_longlong, []),
 }
 
-KERNEL_CLASSES = ["panel", "rowmoves", "trsm", "update", "panelgemm", "trsv", "residual", "lookahead"]
-# classes that time a stretch of the critical path rather than kernels of one kind
-SPAN_CLASSES = ("lookahead",)
+KERNEL_CLASSES = ["panel", "rowmoves", "trsm", "update", "panelgemm", "trsv", "residual"]
 
 
 def profile_enable(classes=()):
@@ -247,11 +245,10 @@ def workspace(nbytes: int, device=None):
 
 
 def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fallback=True,
-         nb_outer=0, gmres_restart=30, gmres_tol=1e-6, work=None, stream=None, lookahead=-1):
+         nb_outer=0, gmres_restart=30, gmres_tol=1e-6, work=None, stream=None):
     """Solve A X = B (Algorithm 1).  A: (n, n) float64 CUDA tensor, B: (n,) or
-    (n, nrhs).  lookahead: the factorization's outer look-ahead on the
-    tensor-core rungs (-1 auto, 0 off, 1 on).  Returns (X, ipiv, stats) with X
-    column-major float64 and ipiv int32 (LAPACK 1-based)."""
+    (n, nrhs).  Returns (X, ipiv, stats) with X column-major float64 and ipiv
+    int32 (LAPACK 1-based)."""
     torch = _torch()
     lib = load()
     A = colmajor(A)
@@ -260,7 +257,7 @@ def gesv(A, B, prec="fp32", refine="classical", itermax=30, tol=1e-14, allow_fal
     n, nrhs = B.shape
     opts = default_opts(prec=prec, refine=refine, itermax=itermax, tol=tol,
                         allow_fallback=int(bool(allow_fallback)), nb_outer=nb_outer,
-                        gmres_restart=gmres_restart, gmres_tol=gmres_tol, lookahead=lookahead)
+                        gmres_restart=gmres_restart, gmres_tol=gmres_tol)
     X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
     ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     need = lib.mp_gesv_workspace_bytes(n, nrhs, ctypes.byref(opts))
@@ -481,14 +478,13 @@ def convert(A, work=None, stream=None):
     return W, anorm, flags
 
 
-def getrf_lowp(W, prec="fp32", nb_outer=0, work=None, stream=None, lookahead=-1):
+def getrf_lowp(W, prec="fp32", nb_outer=0, work=None, stream=None):
     """In-place LU with partial pivoting of the row-major FP32 W (n x ldw).
-    lookahead: the outer look-ahead on the tensor-core rungs (-1 auto, 0 off,
-    1 on).  Returns (ipiv, info, flags)."""
+    Returns (ipiv, info, flags)."""
     torch = _torch()
     lib = load()
     n, ldw = W.shape
-    opts = default_opts(prec=prec, nb_outer=nb_outer, lookahead=lookahead)
+    opts = default_opts(prec=prec, nb_outer=nb_outer)
     ipiv = torch.zeros(max(n, 1), dtype=torch.int32, device=W.device)
     need = lib.mp_getrf_workspace_bytes(n, ctypes.byref(opts))
     if work is None or work.numel() < need:
