@@ -36,3 +36,24 @@ def test_class_rooflines_bounds_and_units():
 def test_class_rooflines_fp32_update_is_alu():
     r = bench.class_rooflines({"update": (100.0, 64, 2.9e12)}, PEAKS, "fp32", 16384, 1)
     assert r["update"]["bound"] == "alu"
+
+
+def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The traffic figure of a class is read from the profile table only while
+    the kernel's source file still has the hash recorded at capture time; once
+    the file changes, the bench reports no traffic and says why."""
+    src = tmp_path / "paper_0808_2794_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "panel.cu").write_text("// kernel source at capture time\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.source_sha16("paper_0808_2794_gb300/csrc/panel.cu")
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.md").write_text(
+        "| class | kernel | source | sha16 | workload | launches | bytes/launch |\n|---|---|---|---|---|---|---|\n"
+        f"| panel | panel_getf2_kernel | paper_0808_2794_gb300/csrc/panel.cu | {sha} | test | 3 | 2.5e+06 |\n")
+    value, why = bench.recorded_traffic("panel")
+    assert value == 2.5e6 and "test" in why
+    (src / "panel.cu").write_text("// kernel source changed since\n")
+    value, why = bench.recorded_traffic("panel")
+    assert value is None and "changed" in why
+    assert bench.recorded_traffic("no_such_class") == (None, None)
